@@ -1,0 +1,354 @@
+"""Benchmark: CVA fit + projection + 8-bit rescale on a synthetic manuscript cube.
+
+One step = one pass of the whole path on one cube already resident in HBM:
+class moments of the training pixels, FP64 scatter and eigensolve, training
+ranges, and the fused projection + 8-bit rescale of every pixel onto the top
+canonical variates.  ``value`` is Mpixel/s of whole steps (all ranks), timed
+with CUDA events on the launching stream; ``e2e`` repeats the step through the
+Python binding with the cube and labels copied from pinned host memory and the
+8-bit images copied back inside the timed region.
+
+``--impl reference`` times the FP64 CPU oracle instead, on a bounded sample
+of each step, on the host cores.
+
+Multi-GPU (torchrun): every rank processes its own page (pages are
+independent problems), no data-path collective; the timing is the max over
+ranks and the value counts all ranks' pixels.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CVA Mpixel/s (fit+project) & % HBM roofline; mixed vs FP64 path at ≤1e-4 err"
+UNIT = "Mpixel/s"
+DEFAULT_WORKLOAD = "cube23b_4096x4096_K4"
+L2_BYTES = 126 * 1024 * 1024
+
+# DRAM traffic of one k_project_v8<3, u8> launch on the 23-band 4096 x 4096
+# cube, from ncu (dram__bytes_read.sum + dram__bytes_write.sum), valid while
+# the projection source hashes to PROJECT_SRC_SHA256; null otherwise.
+PROJECT_TRAFFIC_BYTES = None
+PROJECT_SRC_SHA256 = None
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _workload(name, rank):
+    from synth import named_workload
+
+    return named_workload(name)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_hash():
+    with open(os.path.join(ROOT, "paper_1612_06457_gb300", "csrc", "project.cu"), "rb") as f:
+        h = hashlib.sha256(f.read())
+    with open(os.path.join(ROOT, "paper_1612_06457_gb300", "csrc", "cva_internal.cuh"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        loaded = [r for r in rows if (num(r[4]) or 0) > 0] or rows
+        sm = [num(r[1]) for r in loaded if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(rows[0][2]),
+                "reasons": reasons, "samples": len(loaded),
+                "power_w_max": max((num(r[3]) or 0) for r in loaded)}
+
+
+def _oracle_step_time(w, rows):
+    """Oracle fit on the whole cube plus projection, training range and 8-bit
+    rescale of the first `rows` image rows; returns (t_fit, t_rows)."""
+    import numpy as np
+
+    import oracle
+
+    t0 = time.perf_counter()
+    f = oracle.fit(w.cube, w.labels, w.K)
+    y_tr = None
+    lab = w.labels.reshape(-1)
+    tr_idx = np.flatnonzero(lab)
+    # the training range needs the training pixels' scores
+    sub = w.cube.reshape(w.B, -1)[:, tr_idx]
+    y_tr = oracle.project(sub.reshape(w.B, 1, -1), f["V"], f["mu"], w.k)
+    rng = oracle.range_global(y_tr)
+    t1 = time.perf_counter()
+    p1 = rows * w.W
+    y = oracle.project(w.cube, f["V"], f["mu"], w.k, 0, p1)
+    oracle.to_u8(y, rng)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def run_reference(a):
+    world, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    w = _workload(a.workload, 0)
+    rows = max(1, min(w.H, 256 * 4096 // max(w.W, 1)))
+    times = []
+    for i in range(a.warmup + a.steps):
+        tf, tr = _oracle_step_time(w, rows)
+        if i >= a.warmup:
+            times.append(tf + tr * (w.H / rows))
+    t = statistics.median(times)
+    value = w.P / t / 1e6
+    sample = (f"each step: oracle fit on all {w.P} pixels ({sum(w.n_train)} training) + projection/8-bit rescale of "
+              f"{rows} of {w.H} rows, scaled to the full image")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(w):
+    return {"workload": w.name, "bands": w.B, "H": w.H, "W": w.W, "classes": w.K,
+            "train_pixels": list(w.n_train), "variates": w.k, "range": "training-score (second rescale)",
+            "l2": f"inputs larger than L2 ({(w.cube.nbytes + w.labels.nbytes) / 1e6:.0f} MB > {L2_BYTES / 2**20:.0f} MiB)"}
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import paper_1612_06457_gb300 as cva
+
+    world, rank, local = _dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    cva.load()
+
+    w = _workload(a.workload, rank)
+    cube_h = torch.from_numpy(w.cube).pin_memory()
+    lab_h = torch.from_numpy(w.labels).pin_memory()
+    cube = cube_h.to(dev)
+    labels = lab_h.to(dev)
+    out = torch.empty((w.k, w.H, w.W), dtype=torch.uint8, device=dev)
+    m = cva.Model(w.B, w.K)
+    cva.cva_set_variates(m, w.k)
+    stream = torch.cuda.Stream(device=dev)
+    P = w.P
+
+    def step(ev_a=None, ev_b=None):
+        cva.cva_fit(cube, labels, w.K, m, stream=stream)
+        if ev_a is not None:
+            ev_a.record(stream)
+        cva.cva_project_u8(cube, m, w.k, cva.CVA_RANGE_TRAINING, out, stream=stream)
+        if ev_b is not None:
+            ev_b.record(stream)
+
+    with torch.cuda.stream(stream):
+        step()
+    torch.cuda.synchronize()
+    st = cva.cva_status(m, stream=stream)
+    if st != cva.CVA_OK:
+        raise SystemExit(f"fit failed: {cva.cva_strerror(st)}")
+
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    if rank == 0:
+        sampler.start()
+    for _ in range(a.warmup):
+        step()
+    pa = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    pb = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for i in range(a.steps):
+        step(pa[i], pb[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if rank == 0 else None
+    ms = t0.elapsed_time(t1) / a.steps
+    proj_ms = statistics.mean(pa[i].elapsed_time(pb[i]) for i in range(a.steps))
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the binding: pinned host -> device, step, images -> host
+    e2e_steps = a.e2e_steps if a.e2e_steps is not None else max(3, min(a.steps, 20))
+    out_h = torch.empty((w.k, w.H, w.W), dtype=torch.uint8).pin_memory()
+    cube_e = torch.empty_like(cube)
+    lab_e = torch.empty_like(labels)
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            cube_e.copy_(cube_h, non_blocking=True)
+            lab_e.copy_(lab_h, non_blocking=True)
+            cva.cva_fit(cube_e, lab_e, w.K, m, stream=stream)
+            cva.cva_project_u8(cube_e, m, w.k, cva.CVA_RANGE_TRAINING, out, stream=stream)
+            out_h.copy_(out, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    st = cva.cva_status(m, stream=stream)
+    if st != cva.CVA_OK:
+        raise SystemExit(f"fit failed during timing: {cva.cva_strerror(st)}")
+
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        alg_bytes = P * (2 * w.B + w.k)
+        achieved = alg_bytes / (proj_ms * 1e-3) / 1e9
+        traffic = PROJECT_TRAFFIC_BYTES if (PROJECT_SRC_SHA256 == _src_hash() and w.name == DEFAULT_WORKLOAD) else None
+        launches_per_step = 3 + (w.k + 7) // 8  # moments, finalize, training range x chunks, projection
+        launches_per_step += 0  # the projection has no tail launch when P % 8 == 0
+        if P % 8:
+            launches_per_step += (w.k + 7) // 8
+        line = {
+            "metric": METRIC, "value": world * P / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(w),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_project_v8 (fused u8)",
+                         "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                         "launch_ms": proj_ms},
+            "e2e": {"value": world * P / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+                    "h2d_bytes_per_step": int(w.cube.nbytes + w.labels.nbytes),
+                    "d2h_bytes_per_step": int(out_h.numel()), "ms_per_step": e2e_ms, "steps": e2e_steps},
+            "gpu_launches": launches_per_step * a.steps,
+            "clocks": clocks,
+            "fit_ms": ms - proj_ms,
+        }
+        if not a.no_cpu_baseline and world == 1:
+            rows = max(1, min(w.H, 256 * 4096 // max(w.W, 1)))
+            tf, tr = _oracle_step_time(w, rows)
+            t = tf + tr * (w.H / rows)
+            line["cpu_baseline"] = {
+                "value": P / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": (f"oracle fit on all {P} pixels + projection/8-bit rescale of {rows} of {w.H} rows "
+                           f"({tf:.2f} s + {tr:.2f} s), scaled to the full image")}
+        print(json.dumps(line), flush=True)
+    m.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * cva.h -- C ABI of the GB300 (sm_103a) Canonical Variates Analysis library.
+ *
+ * The library fits Canonical Variates Analysis (CVA) to the labelled training
+ * pixels of a multispectral cube and projects every pixel of the cube onto
+ * the top canonical variates, rescaled to 8-bit images, as described in
+ * arXiv 1612.06457 (Arsene, Church, Dickinson), Section 2 (the method and
+ * the three rescales) and Section 4 (the generalized symmetric-definite
+ * eigenproblem solved by GSL, and the eigenvector sign ambiguity).
+ *
+ * Conventions shared by every call:
+ *   - Data pointers marked "device" must point to device memory of the
+ *     current CUDA device; the caller owns them.  Host pointers are marked
+ *     "host".  The library owns only its model objects.
+ *   - cube: uint16, band-sequential (band-major), B x H x W, band b of pixel
+ *     p = y W + x at cube[b H W + p].  Band 0 is the first band of the stack.
+ *   - labels: uint8, H x W, 0 = not a training pixel, c + 1 = training pixel
+ *     of class c (0 <= c < K).
+ *   - projections: float32 k x H x W (variate-major); 8-bit images: uint8
+ *     k x H x W; ranges: 2 k float32 as (lo_0, hi_0, lo_1, hi_1, ...).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call that takes a stream is asynchronous on it unless
+ *     its comment says it synchronizes.
+ *   - Return value: CVA_OK (0) or a negative CVA_ERR_* code.  Argument errors
+ *     are detected on the host and returned at once, before any launch.
+ *     Errors found on the device (an empty class, a label above K, Sw not
+ *     positive definite, no convergence) are written to the model's status
+ *     word; cva_status() and cva_model_get() return them.  Projections from
+ *     a model whose fit failed leave their outputs untouched.
+ *   - Limits: 1 <= B <= CVA_MAX_BANDS, 2 <= K <= CVA_MAX_CLASSES,
+ *     1 <= H, W and H W < 2^31, 1 <= k <= B.
+ */
+#ifndef CVA_H_
+#define CVA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CVA_MAX_BANDS 32
+#define CVA_MAX_CLASSES 16
+
+#define CVA_OK 0
+#define CVA_ERR_INVALID_ARG (-1)    /* bad size, pointer, mode or alignment */
+#define CVA_ERR_EMPTY_CLASS (-2)    /* a class has no training pixel */
+#define CVA_ERR_NOT_SPD (-3)        /* within-class scatter not positive definite */
+#define CVA_ERR_NO_CONVERGENCE (-4) /* eigensolver hit its sweep limit */
+#define CVA_ERR_TIMEOUT (-5)        /* a bounded device-side wait gave up */
+#define CVA_ERR_CUDA (-6)           /* a CUDA runtime call failed */
+#define CVA_ERR_LABEL_RANGE (-7)    /* a label is above K */
+#define CVA_ERR_NOT_FITTED (-8)     /* the model has not been fitted */
+
+/* Which range maps a projection onto 0..255 (Section 2 gives the first two). */
+typedef enum {
+    CVA_RANGE_GLOBAL = 0,   /* min / max over every pixel of the projection */
+    CVA_RANGE_TRAINING = 1, /* min / max over the training pixels' scores */
+    CVA_RANGE_GIVEN = 2     /* a caller-supplied range */
+} cva_range_mode;
+
+/* Arithmetic of the fit and the projection. */
+typedef enum {
+    /* Class moments in exact 64-bit integer arithmetic, FP64 scatter,
+     * eigensolve and coefficients, FP32 projection. */
+    CVA_PRECISION_EXACT = 0,
+    /* Class means first (exact), then the within-class scatter from BF16
+     * hi/lo split mean-shifted values on the tensor cores with FP32
+     * accumulation, merged in FP64; projection from BF16 hi/lo split
+     * operands on the tensor cores with FP32 accumulation. */
+    CVA_PRECISION_SPLIT_BF16 = 1
+} cva_precision_mode;
+
+typedef struct cva_model cva_model;
+
+/* Create a model for B bands and K classes on the current CUDA device.  Owns
+ * a small device block (a few hundred KB) until cva_model_destroy.  *out is
+ * set to NULL on error.  Not stream-ordered: allocates with cudaMalloc, so
+ * call it outside stream capture. */
+int cva_model_create(int B, int K, cva_model** out);
+
+/* Free the model (synchronizes the device first).  NULL is a no-op. */
+void cva_model_destroy(cva_model* m);
+
+/* Select CVA_PRECISION_EXACT (default) or CVA_PRECISION_SPLIT_BF16 for the
+ * following fits and projections. */
+int cva_set_precision(cva_model* m, int mode);
+
+/* Number of canonical vectors, with their training-score ranges, that each
+ * following fit forms: 1 <= nvec <= B (default B).  Projections take
+ * k <= nvec.  The first min(K-1, B) vectors solve the eigenproblem with
+ * non-zero eigenvalues; any further ones complete the basis of the
+ * eigenvalue-0 space (V^T Sw V = I still holds) and are not unique. */
+int cva_set_variates(cva_model* m, int nvec);
+
+/* Fit (Section 2: within-class and between-class scatter of the labelled
+ * training pixels and their eigenanalysis; Section 4: Sb v = lambda Sw v).
+ *   cube   device, B x H x W uint16 (2-byte aligned)
+ *   labels device, H x W uint8 (0 = unlabelled, c + 1 = class c)
+ * Results stay in the model on the device: eigenvalues lambda in descending
+ * order, eigenvectors V with V^T Sw V = I and the largest-magnitude
+ * component of each positive (lowest band on a tie), the training mean, and
+ * the training-score range of each variate.  Sw and Sb are unnormalised
+ * sums of squares and cross-products.  Forms the number of vectors set by
+ * cva_set_variates.  Only kernel launches and one memset on `stream`: no
+ * host synchronization and no allocation. */
+int cva_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, int K,
+            cva_model* m, void* stream);
+
+/* Synchronize `stream` and return the model's device status (CVA_OK or the
+ * first device-side error of the last fit). */
+int cva_status(cva_model* m, void* stream);
+
+/* Copy the fitted model to host memory; synchronizes `stream`.  Any pointer
+ * may be NULL to skip that output.
+ *   eigvals      host, B doubles (descending; 0 beyond the first min(K-1, B))
+ *   V            host, B x B doubles, row-major, column j = canonical vector j
+ *                (columns j >= nvec, see cva_set_variates, are 0)
+ *   mean         host, B doubles (mean of all training pixels)
+ *   train_range  host, 2 B floats: training-score (lo, hi) of each variate
+ *                (+inf, -inf for j >= nvec)
+ * Returns the model's device status, or CVA_ERR_NOT_FITTED. */
+int cva_model_get(cva_model* m, double* eigvals, double* V, double* mean, float* train_range,
+                  void* stream);
+
+/* Copy the fit's intermediate statistics to host memory; synchronizes.
+ *   counts       host, K int64 training pixels per class
+ *   class_means  host, K x B doubles
+ *   Sw, Sb       host, B x B doubles each (row-major)
+ * Any pointer may be NULL.  Returns the model's device status. */
+int cva_model_get_scatter(cva_model* m, int64_t* counts, double* class_means, double* Sw,
+                          double* Sb, void* stream);
+
+/* Projection (Section 2: the canonical coefficients multiplied with the band
+ * images): out_f32[j][p] = sum_b V[b][j] (x_b[p] - mean_b) for j < k.
+ *   out_f32   device, k x H x W float32, or NULL
+ *   range_out device, 2 k float32, or NULL: receives the (lo, hi) of each
+ *             projection over all pixels (the first rescale's range)
+ * At least one of out_f32 / range_out must be non-NULL. */
+int cva_project(const uint16_t* cube, int B, int H, int W, cva_model* m, int k,
+                float* out_f32, float* range_out, void* stream);
+
+/* Rescale projections to 8 bits (Section 2):
+ * out = clamp(floor(255 (y - lo) / (hi - lo) + 1/2), 0, 255), 0 if hi <= lo.
+ *   proj  device, k x H x W float32 from cva_project
+ *   mode  CVA_RANGE_GLOBAL (range computed here from proj, into the model's
+ *         scratch range), CVA_RANGE_TRAINING (range from the model), or
+ *         CVA_RANGE_GIVEN (range = device 2 k float32)
+ *   m     required for CVA_RANGE_GLOBAL and CVA_RANGE_TRAINING; may be NULL
+ *         for CVA_RANGE_GIVEN
+ *   out   device, k x H x W uint8 */
+int cva_to_u8(const float* proj, int k, int H, int W, int mode, const float* range,
+              cva_model* m, uint8_t* out, void* stream);
+
+/* Fused projection and 8-bit rescale: one pass over the cube for
+ * CVA_RANGE_TRAINING and CVA_RANGE_GIVEN, two passes (range, then
+ * projection) for CVA_RANGE_GLOBAL.
+ *   range device, 2 k float32 for CVA_RANGE_GIVEN, else NULL
+ *   out   device, k x H x W uint8 */
+int cva_project_u8(const uint16_t* cube, int B, int H, int W, cva_model* m, int k, int mode,
+                   const float* range, uint8_t* out, void* stream);
+
+/* Human-readable text of a CVA_* code (static storage). */
+const char* cva_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CVA_H_ */

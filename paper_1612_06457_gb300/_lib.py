@@ -1,0 +1,221 @@
+"""ctypes binding of the C ABI in include/cva.h.
+
+Argument marshalling only: every computation runs in the CUDA kernels of
+``libcva.so``.  Functions keep the C names; where the C call takes a device
+pointer plus its sizes, the binding takes a CUDA tensor and reads the sizes
+from its shape.  A missing library raises at import time of the binding,
+never falls back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+from . import _build
+
+CVA_OK = 0
+CVA_ERR_INVALID_ARG = -1
+CVA_ERR_EMPTY_CLASS = -2
+CVA_ERR_NOT_SPD = -3
+CVA_ERR_NO_CONVERGENCE = -4
+CVA_ERR_TIMEOUT = -5
+CVA_ERR_CUDA = -6
+CVA_ERR_LABEL_RANGE = -7
+CVA_ERR_NOT_FITTED = -8
+
+CVA_RANGE_GLOBAL = 0
+CVA_RANGE_TRAINING = 1
+CVA_RANGE_GIVEN = 2
+
+CVA_PRECISION_EXACT = 0
+CVA_PRECISION_SPLIT_BF16 = 1
+
+CVA_MAX_BANDS = 32
+CVA_MAX_CLASSES = 16
+
+# name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+SIGNATURES = {
+    "cva_model_create": (_I, [_I, _I, ctypes.POINTER(_P)]),
+    "cva_model_destroy": (None, [_P]),
+    "cva_set_precision": (_I, [_P, _I]),
+    "cva_set_variates": (_I, [_P, _I]),
+    "cva_fit": (_I, [_P, _I, _I, _I, _P, _I, _P, _P]),
+    "cva_status": (_I, [_P, _P]),
+    "cva_model_get": (_I, [_P, _P, _P, _P, _P, _P]),
+    "cva_model_get_scatter": (_I, [_P, _P, _P, _P, _P, _P]),
+    "cva_project": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P]),
+    "cva_to_u8": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "cva_project_u8": (_I, [_P, _I, _I, _I, _P, _I, _I, _P, _P, _P]),
+    "cva_strerror": (ctypes.c_char_p, [_I]),
+}
+
+_lib = None
+
+
+class CvaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {cva_strerror(code)} ({code})")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcva.so (building it first if it is missing or stale and
+    ``build_if_missing`` is set)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and _build.stale():
+        _build.build()
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} is missing (run paper_1612_06457_gb300.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str) -> None:
+    if code != CVA_OK:
+        raise CvaError(code, where)
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t: Optional[torch.Tensor], dtype: torch.dtype, name: str):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or t.dtype != dtype:
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def cva_strerror(code: int) -> str:
+    return load().cva_strerror(code).decode()
+
+
+class Model:
+    """Owner of one ``cva_model`` handle."""
+
+    def __init__(self, B: int, K: int):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.cva_model_create(B, K, ctypes.byref(h)), "cva_model_create")
+        self.handle = h
+        self.B = B
+        self.K = K
+        self.nvec = B
+
+    def close(self) -> None:
+        if self.handle:
+            load().cva_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cva_model_create(B: int, K: int) -> Model:
+    return Model(B, K)
+
+
+def cva_model_destroy(m: Model) -> None:
+    m.close()
+
+
+def cva_set_precision(m: Model, mode: int) -> None:
+    _check(load().cva_set_precision(m.handle, mode), "cva_set_precision")
+
+
+def cva_set_variates(m: Model, nvec: int) -> None:
+    _check(load().cva_set_variates(m.handle, nvec), "cva_set_variates")
+    m.nvec = nvec
+
+
+def cva_fit(cube: torch.Tensor, labels: torch.Tensor, K: int, m: Model, stream=None) -> None:
+    B, H, W = cube.shape
+    if tuple(labels.shape) != (H, W):
+        raise ValueError("labels must be H x W")
+    rc = load().cva_fit(_dptr(cube, torch.uint16, "cube"), B, H, W, _dptr(labels, torch.uint8, "labels"),
+                        K, m.handle, _stream_ptr(stream))
+    _check(rc, "cva_fit")
+
+
+def cva_status(m: Model, stream=None) -> int:
+    return load().cva_status(m.handle, _stream_ptr(stream))
+
+
+def cva_model_get(m: Model, stream=None):
+    """Returns (eigvals [B], V [B, B], mean [B], train_range [2B]) as numpy."""
+    import numpy as np
+
+    B = m.B
+    lam = np.zeros(B)
+    V = np.zeros((B, B))
+    mean = np.zeros(B)
+    rng = np.zeros(2 * B, np.float32)
+    _check(load().cva_model_get(m.handle, _hptr(lam), _hptr(V), _hptr(mean), _hptr(rng), _stream_ptr(stream)),
+           "cva_model_get")
+    return lam, V, mean, rng
+
+
+def cva_model_get_scatter(m: Model, stream=None):
+    """Returns (counts [K], class_means [K, B], Sw [B, B], Sb [B, B]) as numpy."""
+    import numpy as np
+
+    B, K = m.B, m.K
+    n = np.zeros(K, np.int64)
+    mc = np.zeros((K, B))
+    Sw = np.zeros((B, B))
+    Sb = np.zeros((B, B))
+    _check(load().cva_model_get_scatter(m.handle, _hptr(n), _hptr(mc), _hptr(Sw), _hptr(Sb), _stream_ptr(stream)),
+           "cva_model_get_scatter")
+    return n, mc, Sw, Sb
+
+
+def cva_project(cube: torch.Tensor, m: Model, k: int, out_f32: Optional[torch.Tensor] = None,
+                range_out: Optional[torch.Tensor] = None, stream=None) -> None:
+    B, H, W = cube.shape
+    rc = load().cva_project(_dptr(cube, torch.uint16, "cube"), B, H, W, m.handle, k,
+                            _dptr(out_f32, torch.float32, "out_f32"), _dptr(range_out, torch.float32, "range_out"),
+                            _stream_ptr(stream))
+    _check(rc, "cva_project")
+
+
+def cva_to_u8(proj: torch.Tensor, mode: int, out: torch.Tensor, m: Optional[Model] = None,
+              range: Optional[torch.Tensor] = None, stream=None) -> None:
+    k, H, W = proj.shape
+    rc = load().cva_to_u8(_dptr(proj, torch.float32, "proj"), k, H, W, mode, _dptr(range, torch.float32, "range"),
+                          m.handle if m is not None else None, _dptr(out, torch.uint8, "out"), _stream_ptr(stream))
+    _check(rc, "cva_to_u8")
+
+
+def cva_project_u8(cube: torch.Tensor, m: Model, k: int, mode: int, out: torch.Tensor,
+                   range: Optional[torch.Tensor] = None, stream=None) -> None:
+    B, H, W = cube.shape
+    rc = load().cva_project_u8(_dptr(cube, torch.uint16, "cube"), B, H, W, m.handle, k, mode,
+                               _dptr(range, torch.float32, "range"), _dptr(out, torch.uint8, "out"),
+                               _stream_ptr(stream))
+    _check(rc, "cva_project_u8")

@@ -1,0 +1,292 @@
+// cva_abi.cu -- the extern "C" entry points declared in include/cva.h.
+//
+// Host-side argument checks, then kernel launches on the caller's stream.
+// The model object owns one DevModel block in device memory; the caller owns
+// every cube, label, projection and image buffer.
+#include <cstddef>
+#include <cstring>
+#include <new>
+
+#include "cva_internal.cuh"
+
+struct cva_model {
+    int B;
+    int K;
+    int device;
+    int num_sms;
+    int nvec;
+    int precision;
+    cva::DevModel* dm;
+};
+
+namespace {
+
+using cva::DevModel;
+
+int from_cuda(cudaError_t e)
+{
+    return e == cudaSuccess ? CVA_OK : CVA_ERR_CUDA;
+}
+
+// A pointer the GPU can read: device or managed memory, or host memory that
+// is registered / mapped.  Plain pageable host memory is refused.
+bool device_visible(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
+           (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr);
+}
+
+bool valid_dims(int B, int H, int W)
+{
+    if (B < 1 || B > CVA_MAX_BANDS || H < 1 || W < 1) return false;
+    const long long P = static_cast<long long>(H) * W;
+    return P < (1LL << 31);
+}
+
+int read_status(cva_model* m, cudaStream_t s, int* fitted)
+{
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return CVA_ERR_CUDA;
+    int st[2] = {0, 0};
+    e = cudaMemcpy(st, &m->dm->status, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return CVA_ERR_CUDA;
+    if (fitted) *fitted = st[1];
+    return st[0];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cva_strerror(int code)
+{
+    switch (code) {
+        case CVA_OK: return "success";
+        case CVA_ERR_INVALID_ARG: return "invalid argument";
+        case CVA_ERR_EMPTY_CLASS: return "a class has no training pixel";
+        case CVA_ERR_NOT_SPD: return "within-class scatter is not positive definite";
+        case CVA_ERR_NO_CONVERGENCE: return "eigensolver did not converge";
+        case CVA_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case CVA_ERR_CUDA: return "CUDA runtime error";
+        case CVA_ERR_LABEL_RANGE: return "a label is above the class count";
+        case CVA_ERR_NOT_FITTED: return "model not fitted";
+        default: return "unknown error";
+    }
+}
+
+int cva_model_create(int B, int K, cva_model** out)
+{
+    if (!out) return CVA_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (B < 1 || B > CVA_MAX_BANDS || K < 2 || K > CVA_MAX_CLASSES) return CVA_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CVA_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CVA_ERR_CUDA;
+    DevModel* dm = nullptr;
+    if (cudaMalloc(&dm, sizeof(DevModel)) != cudaSuccess) return CVA_ERR_CUDA;
+    if (cudaMemset(dm, 0, sizeof(DevModel)) != cudaSuccess) {
+        cudaFree(dm);
+        return CVA_ERR_CUDA;
+    }
+    cva_model* m = new (std::nothrow) cva_model;
+    if (!m) {
+        cudaFree(dm);
+        return CVA_ERR_INVALID_ARG;
+    }
+    m->B = B;
+    m->K = K;
+    m->device = dev;
+    m->num_sms = sms;
+    m->nvec = B;
+    m->precision = CVA_PRECISION_EXACT;
+    m->dm = dm;
+    *out = m;
+    return CVA_OK;
+}
+
+void cva_model_destroy(cva_model* m)
+{
+    if (!m) return;
+    cudaDeviceSynchronize();
+    cudaFree(m->dm);
+    delete m;
+}
+
+int cva_set_precision(cva_model* m, int mode)
+{
+    if (!m || (mode != CVA_PRECISION_EXACT && mode != CVA_PRECISION_SPLIT_BF16)) return CVA_ERR_INVALID_ARG;
+    m->precision = mode;
+    return CVA_OK;
+}
+
+int cva_set_variates(cva_model* m, int nvec)
+{
+    if (!m || nvec < 1 || nvec > m->B) return CVA_ERR_INVALID_ARG;
+    m->nvec = nvec;
+    return CVA_OK;
+}
+
+int cva_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, int K, cva_model* m,
+            void* stream)
+{
+    if (!m || B != m->B || K != m->K || !valid_dims(B, H, W)) return CVA_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(cube) % 2 != 0) return CVA_ERR_INVALID_ARG;
+    if (!device_visible(cube) || !device_visible(labels)) return CVA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long P = static_cast<long long>(H) * W;
+    cudaError_t e = cudaMemsetAsync(m->dm, 0, offsetof(DevModel, n), s);
+    if (e == cudaSuccess) e = cva::launch_fit_moments(cube, B, P, labels, K, m->dm, m->num_sms, s);
+    if (e == cudaSuccess) e = cva::launch_fit_finalize(m->dm, B, K, m->nvec, s);
+    if (e == cudaSuccess) e = cva::launch_train_range(cube, B, P, labels, K, m->dm, m->nvec, m->num_sms, s);
+    return from_cuda(e);
+}
+
+int cva_status(cva_model* m, void* stream)
+{
+    if (!m) return CVA_ERR_INVALID_ARG;
+    return read_status(m, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+int cva_model_get(cva_model* m, double* eigvals, double* V, double* mean, float* train_range, void* stream)
+{
+    if (!m) return CVA_ERR_INVALID_ARG;
+    int fitted = 0;
+    const int st = read_status(m, static_cast<cudaStream_t>(stream), &fitted);
+    if (st != CVA_OK) return st;
+    if (!fitted) return CVA_ERR_NOT_FITTED;
+    const int B = m->B;
+    const DevModel* dm = m->dm;
+    if (eigvals && cudaMemcpy(eigvals, dm->lam, sizeof(double) * B, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    if (mean && cudaMemcpy(mean, dm->mu, sizeof(double) * B, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    if (train_range &&
+        cudaMemcpy(train_range, dm->train_range, sizeof(float) * 2 * B, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    if (V && cudaMemcpy2D(V, sizeof(double) * B, dm->V, sizeof(double) * cva::MAXB, sizeof(double) * B, B,
+                          cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    return CVA_OK;
+}
+
+int cva_model_get_scatter(cva_model* m, int64_t* counts, double* class_means, double* Sw, double* Sb,
+                          void* stream)
+{
+    if (!m) return CVA_ERR_INVALID_ARG;
+    int fitted = 0;
+    const int st = read_status(m, static_cast<cudaStream_t>(stream), &fitted);
+    if (st != CVA_OK) return st;
+    if (!fitted) return CVA_ERR_NOT_FITTED;
+    const int B = m->B, K = m->K;
+    const DevModel* dm = m->dm;
+    if (counts && cudaMemcpy(counts, dm->n, sizeof(int64_t) * K, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    if (class_means && cudaMemcpy2D(class_means, sizeof(double) * B, dm->mu_c, sizeof(double) * cva::MAXB,
+                                    sizeof(double) * B, K, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    if (Sw && cudaMemcpy2D(Sw, sizeof(double) * B, dm->Sw, sizeof(double) * cva::MAXB, sizeof(double) * B, B,
+                           cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    if (Sb && cudaMemcpy2D(Sb, sizeof(double) * B, dm->Sb, sizeof(double) * cva::MAXB, sizeof(double) * B, B,
+                           cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    return CVA_OK;
+}
+
+int cva_project(const uint16_t* cube, int B, int H, int W, cva_model* m, int k, float* out_f32,
+                float* range_out, void* stream)
+{
+    if (!m || B != m->B || !valid_dims(B, H, W) || k < 1 || k > m->nvec) return CVA_ERR_INVALID_ARG;
+    if (!out_f32 && !range_out) return CVA_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(cube) % 2 != 0 || reinterpret_cast<uintptr_t>(out_f32) % 4 != 0 ||
+        reinterpret_cast<uintptr_t>(range_out) % 4 != 0)
+        return CVA_ERR_INVALID_ARG;
+    if (!device_visible(cube) || (out_f32 && !device_visible(out_f32)) || (range_out && !device_visible(range_out)))
+        return CVA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long P = static_cast<long long>(H) * W;
+    cudaError_t e = cudaSuccess;
+    if (range_out) e = cva::launch_range_init(range_out, k, s);
+    if (e == cudaSuccess)
+        e = cva::launch_project(cube, B, P, m->dm, k, out_f32, nullptr, nullptr, range_out, m->num_sms, s);
+    return from_cuda(e);
+}
+
+int cva_to_u8(const float* proj, int k, int H, int W, int mode, const float* range, cva_model* m, uint8_t* out,
+              void* stream)
+{
+    if (k < 1 || k > CVA_MAX_BANDS || H < 1 || W < 1 || static_cast<long long>(H) * W >= (1LL << 31))
+        return CVA_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(proj) % 4 != 0) return CVA_ERR_INVALID_ARG;
+    if (!device_visible(proj) || !device_visible(out)) return CVA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long P = static_cast<long long>(H) * W;
+    cudaError_t e = cudaSuccess;
+    const DevModel* dmc = m ? m->dm : nullptr;
+    switch (mode) {
+        case CVA_RANGE_GLOBAL:
+            if (!m) return CVA_ERR_INVALID_ARG;
+            e = cva::launch_range_init(m->dm->work_range, k, s);
+            if (e == cudaSuccess) e = cva::launch_f32_range(proj, k, P, dmc, m->dm->work_range, m->num_sms, s);
+            if (e == cudaSuccess) e = cva::launch_f32_to_u8(proj, k, P, dmc, m->dm->work_range, out, m->num_sms, s);
+            break;
+        case CVA_RANGE_TRAINING:
+            if (!m || k > m->nvec) return CVA_ERR_INVALID_ARG;
+            e = cva::launch_f32_to_u8(proj, k, P, dmc, m->dm->train_range, out, m->num_sms, s);
+            break;
+        case CVA_RANGE_GIVEN: {
+            if (!range || !device_visible(range) || reinterpret_cast<uintptr_t>(range) % 4 != 0)
+                return CVA_ERR_INVALID_ARG;
+            int sms = 0, dev = 0;
+            if (m) sms = m->num_sms;
+            else if (cudaGetDevice(&dev) != cudaSuccess ||
+                     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return CVA_ERR_CUDA;
+            e = cva::launch_f32_to_u8(proj, k, P, dmc, range, out, sms, s);
+            break;
+        }
+        default:
+            return CVA_ERR_INVALID_ARG;
+    }
+    return from_cuda(e);
+}
+
+int cva_project_u8(const uint16_t* cube, int B, int H, int W, cva_model* m, int k, int mode, const float* range,
+                   uint8_t* out, void* stream)
+{
+    if (!m || B != m->B || !valid_dims(B, H, W) || k < 1 || k > m->nvec) return CVA_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(cube) % 2 != 0) return CVA_ERR_INVALID_ARG;
+    if (!device_visible(cube) || !device_visible(out)) return CVA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long P = static_cast<long long>(H) * W;
+    DevModel* dm = m->dm;
+    cudaError_t e = cudaSuccess;
+    switch (mode) {
+        case CVA_RANGE_TRAINING:
+            e = cva::launch_project(cube, B, P, dm, k, nullptr, out, dm->train_range, nullptr, m->num_sms, s);
+            break;
+        case CVA_RANGE_GIVEN:
+            if (!range || !device_visible(range) || reinterpret_cast<uintptr_t>(range) % 4 != 0)
+                return CVA_ERR_INVALID_ARG;
+            e = cva::launch_project(cube, B, P, dm, k, nullptr, out, range, nullptr, m->num_sms, s);
+            break;
+        case CVA_RANGE_GLOBAL:
+            e = cva::launch_range_init(dm->work_range, k, s);
+            if (e == cudaSuccess)
+                e = cva::launch_project(cube, B, P, dm, k, nullptr, nullptr, nullptr, dm->work_range, m->num_sms, s);
+            if (e == cudaSuccess)
+                e = cva::launch_project(cube, B, P, dm, k, nullptr, out, dm->work_range, nullptr, m->num_sms, s);
+            break;
+        default:
+            return CVA_ERR_INVALID_ARG;
+    }
+    return from_cuda(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// cva_internal.cuh -- device model layout, launch helpers and small device
+// utilities shared by the CUDA translation units of the CVA library.
+//
+// Nothing here is part of the C ABI (include/cva.h); the model block below
+// lives in device memory and is owned by a cva_model.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cva.h"
+
+namespace cva {
+
+constexpr int MAXB = CVA_MAX_BANDS;                     // 32 bands
+constexpr int MAXK = CVA_MAX_CLASSES;                   // 16 classes
+constexpr int MAXBA = ((MAXB + 1 + 3) / 4) * 4;         // augmented bands, padded to 4: 36
+constexpr int MAXNB = MAXBA / 4;                        // 4-band blocks: 9
+constexpr int MAXBLK = MAXNB * (MAXNB + 1) / 2;         // upper-triangle block pairs: 45
+
+// Pivot test of the Cholesky factorization: Sw is "not positive definite"
+// when a pivot is not above this multiple of its own diagonal entry.
+constexpr double PIVOT_REL = 1e-12;
+// Eigenvector sign convention: components within this relative distance of
+// the largest magnitude tie, and the lowest band index wins.
+constexpr double TIE_REL = 1e-12;
+// 2^23 as a float: or-ing a 16-bit integer into its mantissa gives 2^23 + x.
+constexpr float MAGIC_2P23 = 8388608.0f;
+
+// Shape of the augmented moment tiles for B bands: the vector (x_0 .. x_{B-1}, 1)
+// padded with zeros to BP (a multiple of 4) entries, cut into nb blocks of 4.
+struct MomShape {
+    int BA, BP, nb, nblk;
+};
+
+__host__ __device__ inline MomShape mom_shape(int B)
+{
+    MomShape s;
+    s.BA = B + 1;
+    s.BP = (s.BA + 3) & ~3;
+    s.nb = s.BP / 4;
+    s.nblk = s.nb * (s.nb + 1) / 2;
+    return s;
+}
+
+// Index of the 4x4 block pair (bi, bj), bi <= bj, in row-major upper-triangle order.
+__host__ __device__ inline int blk_index(int bi, int bj, int nb)
+{
+    return bi * nb - bi * (bi - 1) / 2 + (bj - bi);
+}
+
+// Device-resident model.  One per cva_model; written by the fit kernels and
+// read by the projection kernels.  All matrices are [row][column].
+struct DevModel {
+    // ---- fit workspace: zeroed at the start of every fit -------------------
+    // Exact integer moments of the augmented training vectors (x, 1) per
+    // class: block pair (bi, bj), slot 4a + b holds sum x'_{4bi+a} x'_{4bj+b}.
+    unsigned long long mom[MAXK][MAXBLK][16];
+    int status;   // CVA_OK or the first device-side error
+    int fitted;   // 1 once a fit finished without error
+    int r;        // eigenpairs taken from the reduced K x K problem
+    int nvec;     // canonical vectors formed (columns of V)
+
+    // ---- fit results --------------------------------------------------------
+    long long n[MAXK];          // training pixels per class
+    double mu_c[MAXK][MAXB];    // class means
+    double mu[MAXB];            // mean of all training pixels
+    double Sw[MAXB][MAXB];      // within-class scatter
+    double Sb[MAXB][MAXB];      // between-class scatter
+    double L[MAXB][MAXB];       // lower Cholesky factor of Sw
+    double Linvd[MAXB];         // 1 / L[i][i]
+    double U[MAXB][MAXB];       // whitened eigenvectors, U = L^T V
+    double lam[MAXB];           // eigenvalues, descending
+    double V[MAXB][MAXB];       // canonical vectors, V[b][j]
+
+    // ---- FP32 projection coefficients ---------------------------------------
+    //   y_j = sum_b Vf[b][j] ((2^23 + x_b) - shift[b]) - dofs[j]
+    // with shift[b] = 2^23 + rint(mu_b) (the centring done exactly in FP32)
+    // and dofs[j] = sum_b V[b][j] (mu_b - rint(mu_b)) rounded once.
+    float Vf[MAXB][MAXB];
+    float shift[MAXB];
+    float dofs[MAXB];
+    float train_range[2 * MAXB];  // (lo, hi) of each variate over the training pixels
+    float work_range[2 * MAXB];   // scratch range for the two-pass global rescale
+};
+
+// -------------------------------------------------------------------------
+// launchers (each defined in the translation unit that holds its kernel)
+// -------------------------------------------------------------------------
+
+cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const uint8_t* labels,
+                               int K, DevModel* dm, int num_sms, cudaStream_t s);
+cudaError_t launch_fit_finalize(DevModel* dm, int B, int K, int nvec, cudaStream_t s);
+cudaError_t launch_train_range(const uint16_t* cube, int B, long long P, const uint8_t* labels,
+                               int K, DevModel* dm, int nvec, int num_sms, cudaStream_t s);
+cudaError_t launch_range_init(float* range, int k, cudaStream_t s);
+cudaError_t launch_project(const uint16_t* cube, int B, long long P, const DevModel* dm, int k,
+                           float* out_f32, uint8_t* out_u8, const float* u8_range,
+                           float* range_acc, int num_sms, cudaStream_t s);
+cudaError_t launch_f32_range(const float* proj, int k, long long P, const DevModel* dm,
+                             float* range_acc, int num_sms, cudaStream_t s);
+cudaError_t launch_f32_to_u8(const float* proj, int k, long long P, const DevModel* dm,
+                             const float* range, uint8_t* out, int num_sms, cudaStream_t s);
+
+// -------------------------------------------------------------------------
+// device helpers
+// -------------------------------------------------------------------------
+
+#ifdef __CUDACC__
+
+// Record the first device-side error of a fit.
+__device__ inline void set_status(DevModel* dm, int code)
+{
+    atomicCAS(&dm->status, 0, code);
+}
+
+// Float min / max on a float stored in global memory, via the ordering of
+// IEEE-754 bit patterns: non-negative floats order like signed integers,
+// negative floats order inversely like unsigned integers.
+__device__ inline void atomic_min_float(float* addr, float v)
+{
+    if (!(v == v)) return;
+    if (__float_as_int(v) >= 0) atomicMin(reinterpret_cast<int*>(addr), __float_as_int(v));
+    else atomicMax(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
+}
+
+__device__ inline void atomic_max_float(float* addr, float v)
+{
+    if (!(v == v)) return;
+    if (__float_as_int(v) >= 0) atomicMax(reinterpret_cast<int*>(addr), __float_as_int(v));
+    else atomicMin(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
+}
+
+// The low (sel = 0) or high (sel = 1) 16-bit half of `w` as the float 2^23 + x:
+// the half's two bytes become the low mantissa bytes under the exponent byte
+// 0x4B of 2^23 (one byte permute, exact).
+__device__ inline float u16_lo_biased(uint32_t w)
+{
+    return __int_as_float(static_cast<int>(__byte_perm(w, 0x4B000000u, 0x7410)));
+}
+__device__ inline float u16_hi_biased(uint32_t w)
+{
+    return __int_as_float(static_cast<int>(__byte_perm(w, 0x4B000000u, 0x7432)));
+}
+__device__ inline float u16_biased(uint32_t x)
+{
+    return __int_as_float(static_cast<int>(0x4B000000u | x));
+}
+
+// 8-bit code of a projection value: floor((y - lo) * scale + 1/2) in 0..255.
+__device__ inline uint32_t to_code(float y, float lo, float scale)
+{
+    float t = __fmaf_rn(__fsub_rn(y, lo), scale, 0.5f);
+    int q = __float2int_rd(t);
+    q = q < 0 ? 0 : q;
+    q = q > 255 ? 255 : q;
+    return static_cast<uint32_t>(q);
+}
+
+// The scale that maps [lo, hi] onto [0, 255]; 0 when the range is empty.
+__device__ inline float code_scale(float lo, float hi)
+{
+    float w = __fsub_rn(hi, lo);
+    return (w > 0.0f && w < 3.0e38f) ? __fdiv_rn(255.0f, w) : 0.0f;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace cva

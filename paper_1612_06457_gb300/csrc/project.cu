@@ -1,0 +1,475 @@
+// project.cu -- projection of every pixel onto the canonical variates and the
+// linear rescale of each projection to 8 bits.
+//
+// Section 2 of the paper multiplies the canonical coefficients with the band
+// images, giving one floating-point image per variate, and maps each onto
+// 0..255 either by its own range over all pixels or by the range of the
+// training points' scores.  Here
+//     y_j[p] = sum_b V[b][j] (x_b[p] - mu_b)
+// is computed in FP32 as
+//     y_j = sum_b Vf[b][j] ((2^23 + x_b) - (2^23 + m_b)) - d_j ,   m_b = rint(mu_b)
+// where 2^23 + x_b is built by one byte permute (no integer-to-float
+// conversion) and the subtraction is exact, so the centring costs nothing and
+// loses nothing; d_j = sum_b V[b][j] (mu_b - m_b) is folded in once.  The
+// 8-bit code is floor((y - lo) * 255 / (hi - lo) + 1/2) clamped to 0..255.
+//
+// The pass is bound by HBM bandwidth (2B bytes in, k or 4k bytes out per
+// pixel): each thread streams 8 consecutive pixels per band with one 16-byte
+// evict-first load, keeps 8 x k FP32 accumulators in registers, and writes
+// 8-byte (u8) or 32-byte (f32) streaming stores.  A scalar kernel covers
+// pixel counts that are not a multiple of 8 and unaligned buffers.
+//
+// The training-range kernel repeats the same FP32 operations, in the same
+// order, on the training pixels, so that the extreme training pixels land on
+// exactly 0 and 255 in the fused projection.
+#include "cva_internal.cuh"
+
+namespace cva {
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int PX = 8;    // pixels per thread per step in the vector path
+constexpr int KCH = 8;   // variates per pass
+constexpr int NWARP = TPB / 32;
+
+template <int KV>
+struct ProjSmem {
+    float V[MAXB][KV];
+    float shift[MAXB];
+    float d[KV];
+    float lo[KV];
+    float scale[KV];
+    float mn[NWARP][KV];
+    float mx[NWARP][KV];
+};
+
+template <int KV>
+__device__ inline void load_coefs(ProjSmem<KV>& sm, const DevModel* dm, int B, int j0, int kc,
+                                  const float* u8_range, bool u8)
+{
+    const int tid = threadIdx.x;
+    for (int e = tid; e < MAXB * KV; e += TPB) {
+        const int b = e / KV, j = e - (e / KV) * KV;
+        sm.V[b][j] = (b < B && j < kc) ? dm->Vf[b][j0 + j] : 0.0f;
+    }
+    if (tid < MAXB) sm.shift[tid] = dm->shift[tid];
+    if (tid < KV) {
+        sm.d[tid] = tid < kc ? dm->dofs[j0 + tid] : 0.0f;
+        float lo = 0.0f, hi = 0.0f;
+        if (u8 && tid < kc) {
+            lo = u8_range[2 * (j0 + tid)];
+            hi = u8_range[2 * (j0 + tid) + 1];
+        }
+        sm.lo[tid] = lo;
+        sm.scale[tid] = code_scale(lo, hi);
+    }
+}
+
+template <int KV>
+__device__ inline void accumulate8(float (&acc)[KV][PX], const uint4& w, const float* vrow, float shift)
+{
+    float x[PX];
+    x[0] = __fsub_rn(u16_lo_biased(w.x), shift);
+    x[1] = __fsub_rn(u16_hi_biased(w.x), shift);
+    x[2] = __fsub_rn(u16_lo_biased(w.y), shift);
+    x[3] = __fsub_rn(u16_hi_biased(w.y), shift);
+    x[4] = __fsub_rn(u16_lo_biased(w.z), shift);
+    x[5] = __fsub_rn(u16_hi_biased(w.z), shift);
+    x[6] = __fsub_rn(u16_lo_biased(w.w), shift);
+    x[7] = __fsub_rn(u16_hi_biased(w.w), shift);
+    #pragma unroll
+    for (int j = 0; j < KV; ++j) {
+        const float v = vrow[j];
+        #pragma unroll
+        for (int i = 0; i < PX; ++i) acc[j][i] = __fmaf_rn(v, x[i], acc[j][i]);
+    }
+}
+
+template <int KV>
+__device__ inline void reduce_range(ProjSmem<KV>& sm, float (&mn)[KV], float (&mx)[KV], int kc,
+                                    float* range_acc, int j0)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    #pragma unroll
+    for (int j = 0; j < KV; ++j) {
+        float a = mn[j], b = mx[j];
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fminf(a, __shfl_xor_sync(0xFFFFFFFFu, a, o));
+            b = fmaxf(b, __shfl_xor_sync(0xFFFFFFFFu, b, o));
+        }
+        if (lane == 0) {
+            sm.mn[warp][j] = a;
+            sm.mx[warp][j] = b;
+        }
+    }
+    __syncthreads();
+    if (tid < kc) {
+        float a = sm.mn[0][tid], b = sm.mx[0][tid];
+        for (int w = 1; w < NWARP; ++w) {
+            a = fminf(a, sm.mn[w][tid]);
+            b = fmaxf(b, sm.mx[w][tid]);
+        }
+        atomic_min_float(range_acc + 2 * (j0 + tid), a);
+        atomic_max_float(range_acc + 2 * (j0 + tid) + 1, b);
+    }
+}
+
+// Vector path: P % 8 == 0 and 16-byte aligned cube (and outputs).
+template <int KV, bool F32, bool U8, bool RNG>
+__global__ void __launch_bounds__(TPB)
+k_project_v8(const uint16_t* __restrict__ cube, int B, long long P, const DevModel* __restrict__ dm,
+             int j0, const float* __restrict__ u8_range, float* __restrict__ out_f32,
+             uint8_t* __restrict__ out_u8, float* __restrict__ range_acc)
+{
+    __shared__ ProjSmem<KV> sm;
+    if (dm->status != 0 || !dm->fitted) return;
+    load_coefs<KV>(sm, dm, B, j0, KV, u8_range, U8);
+    __syncthreads();
+
+    float mn[KV], mx[KV];
+    #pragma unroll
+    for (int j = 0; j < KV; ++j) { mn[j] = __int_as_float(0x7F800000); mx[j] = __int_as_float(0xFF800000); }
+
+    const long long ngroups = P / PX;
+    const long long stride = static_cast<long long>(gridDim.x) * TPB;
+    for (long long g = static_cast<long long>(blockIdx.x) * TPB + threadIdx.x; g < ngroups; g += stride) {
+        const long long p = g * PX;
+        float acc[KV][PX];
+        #pragma unroll
+        for (int j = 0; j < KV; ++j)
+            #pragma unroll
+            for (int i = 0; i < PX; ++i) acc[j][i] = 0.0f;
+        const uint16_t* src = cube + p;
+        int b = 0;
+        for (; b + 4 <= B; b += 4) {
+            uint4 w[4];
+            #pragma unroll
+            for (int u = 0; u < 4; ++u) w[u] = __ldcs(reinterpret_cast<const uint4*>(src + static_cast<long long>(b + u) * P));
+            #pragma unroll
+            for (int u = 0; u < 4; ++u) accumulate8<KV>(acc, w[u], sm.V[b + u], sm.shift[b + u]);
+        }
+        for (; b < B; ++b) {
+            const uint4 w = __ldcs(reinterpret_cast<const uint4*>(src + static_cast<long long>(b) * P));
+            accumulate8<KV>(acc, w, sm.V[b], sm.shift[b]);
+        }
+        #pragma unroll
+        for (int j = 0; j < KV; ++j) {
+            float y[PX];
+            #pragma unroll
+            for (int i = 0; i < PX; ++i) y[i] = __fsub_rn(acc[j][i], sm.d[j]);
+            if (F32) {
+                float4* dst = reinterpret_cast<float4*>(out_f32 + static_cast<long long>(j0 + j) * P + p);
+                __stcs(dst, make_float4(y[0], y[1], y[2], y[3]));
+                __stcs(dst + 1, make_float4(y[4], y[5], y[6], y[7]));
+            }
+            if (U8) {
+                const float lo = sm.lo[j], sc = sm.scale[j];
+                uint32_t c[PX];
+                #pragma unroll
+                for (int i = 0; i < PX; ++i) c[i] = to_code(y[i], lo, sc);
+                const uint2 packed = make_uint2(c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24),
+                                                c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24));
+                __stcs(reinterpret_cast<uint2*>(out_u8 + static_cast<long long>(j0 + j) * P + p), packed);
+            }
+            if (RNG) {
+                #pragma unroll
+                for (int i = 0; i < PX; ++i) { mn[j] = fminf(mn[j], y[i]); mx[j] = fmaxf(mx[j], y[i]); }
+            }
+        }
+    }
+    if (RNG) reduce_range<KV>(sm, mn, mx, KV, range_acc, j0);
+}
+
+// Scalar path: pixels [p_begin, P), one pixel per thread per step, any alignment.
+template <bool F32, bool U8, bool RNG>
+__global__ void __launch_bounds__(TPB)
+k_project_s(const uint16_t* __restrict__ cube, int B, long long P, long long p_begin,
+            const DevModel* __restrict__ dm, int j0, int kc, const float* __restrict__ u8_range,
+            float* __restrict__ out_f32, uint8_t* __restrict__ out_u8, float* __restrict__ range_acc)
+{
+    __shared__ ProjSmem<KCH> sm;
+    if (dm->status != 0 || !dm->fitted) return;
+    load_coefs<KCH>(sm, dm, B, j0, kc, u8_range, U8);
+    __syncthreads();
+    float mn[KCH], mx[KCH];
+    #pragma unroll
+    for (int j = 0; j < KCH; ++j) { mn[j] = __int_as_float(0x7F800000); mx[j] = __int_as_float(0xFF800000); }
+    const long long stride = static_cast<long long>(gridDim.x) * TPB;
+    for (long long p = p_begin + static_cast<long long>(blockIdx.x) * TPB + threadIdx.x; p < P; p += stride) {
+        float acc[KCH];
+        #pragma unroll
+        for (int j = 0; j < KCH; ++j) acc[j] = 0.0f;
+        for (int b = 0; b < B; ++b) {
+            const uint32_t x = __ldcs(cube + static_cast<long long>(b) * P + p);
+            const float xs = __fsub_rn(u16_biased(x), sm.shift[b]);
+            #pragma unroll
+            for (int j = 0; j < KCH; ++j) acc[j] = __fmaf_rn(sm.V[b][j], xs, acc[j]);
+        }
+        #pragma unroll
+        for (int j = 0; j < KCH; ++j) {
+            if (j >= kc) break;
+            const float y = __fsub_rn(acc[j], sm.d[j]);
+            if (F32) out_f32[static_cast<long long>(j0 + j) * P + p] = y;
+            if (U8) out_u8[static_cast<long long>(j0 + j) * P + p] = static_cast<uint8_t>(to_code(y, sm.lo[j], sm.scale[j]));
+            if (RNG) { mn[j] = fminf(mn[j], y); mx[j] = fmaxf(mx[j], y); }
+        }
+    }
+    if (RNG) reduce_range<KCH>(sm, mn, mx, kc, range_acc, j0);
+}
+
+// Training-score range of variates [j0, j0 + kc): same FP32 operations as the
+// projection, on the labelled pixels only.
+__global__ void __launch_bounds__(TPB)
+k_train_range(const uint16_t* __restrict__ cube, int B, long long P, const uint8_t* __restrict__ labels,
+              int K, int vec_labels, DevModel* __restrict__ dm, int j0, int kc)
+{
+    __shared__ ProjSmem<KCH> sm;
+    if (dm->status != 0 || !dm->fitted) return;
+    load_coefs<KCH>(sm, dm, B, j0, kc, nullptr, false);
+    __syncthreads();
+    float mn[KCH], mx[KCH];
+    #pragma unroll
+    for (int j = 0; j < KCH; ++j) { mn[j] = __int_as_float(0x7F800000); mx[j] = __int_as_float(0xFF800000); }
+    constexpr int TILE = TPB * 16;
+    for (long long tile = blockIdx.x; tile * TILE < P; tile += gridDim.x) {
+        const long long p0 = tile * TILE + 16LL * threadIdx.x;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (vec_labels && p0 + 16 <= P) {
+            const uint4 v = __ldcs(reinterpret_cast<const uint4*>(labels + p0));
+            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+        } else {
+            for (int i = 0; i < 16; ++i)
+                if (p0 + i < P) w[i >> 2] |= static_cast<uint32_t>(labels[p0 + i]) << (8 * (i & 3));
+        }
+        if ((w[0] | w[1] | w[2] | w[3]) == 0u) continue;
+        for (int i = 0; i < 16; ++i) {
+            const uint32_t l = (w[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+            if (l == 0u || l > static_cast<uint32_t>(K)) continue;
+            const long long p = p0 + i;
+            float acc[KCH];
+            #pragma unroll
+            for (int j = 0; j < KCH; ++j) acc[j] = 0.0f;
+            for (int b = 0; b < B; ++b) {
+                const uint32_t x = __ldg(cube + static_cast<long long>(b) * P + p);
+                const float xs = __fsub_rn(u16_biased(x), sm.shift[b]);
+                #pragma unroll
+                for (int j = 0; j < KCH; ++j) acc[j] = __fmaf_rn(sm.V[b][j], xs, acc[j]);
+            }
+            #pragma unroll
+            for (int j = 0; j < KCH; ++j) {
+                const float y = __fsub_rn(acc[j], sm.d[j]);
+                mn[j] = fminf(mn[j], y);
+                mx[j] = fmaxf(mx[j], y);
+            }
+        }
+    }
+    reduce_range<KCH>(sm, mn, mx, kc, dm->train_range, j0);
+}
+
+__global__ void k_range_init(float* range, int k)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) {
+        range[2 * j] = __int_as_float(0x7F800000);
+        range[2 * j + 1] = __int_as_float(0xFF800000);
+    }
+}
+
+// Range of FP32 projections (k x P), 4 pixels per thread where aligned.
+__global__ void __launch_bounds__(TPB)
+k_f32_range(const float* __restrict__ proj, int k, long long P, int vec, float* __restrict__ range_acc)
+{
+    __shared__ float smn[NWARP], smx[NWARP];
+    const int j = blockIdx.y;
+    const float* src = proj + static_cast<long long>(j) * P;
+    float a = __int_as_float(0x7F800000), b = __int_as_float(0xFF800000);
+    const long long stride = static_cast<long long>(gridDim.x) * TPB;
+    const long long start = static_cast<long long>(blockIdx.x) * TPB + threadIdx.x;
+    long long done = 0;
+    if (vec) {
+        const long long n4 = P / 4;
+        for (long long g = start; g < n4; g += stride) {
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(src) + g);
+            a = fminf(fminf(a, v.x), fminf(v.y, fminf(v.z, v.w)));
+            b = fmaxf(fmaxf(b, v.x), fmaxf(v.y, fmaxf(v.z, v.w)));
+        }
+        done = n4 * 4;
+    }
+    for (long long p = done + start; p < P; p += stride) {
+        const float v = src[p];
+        a = fminf(a, v);
+        b = fmaxf(b, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fminf(a, __shfl_xor_sync(0xFFFFFFFFu, a, o));
+        b = fmaxf(b, __shfl_xor_sync(0xFFFFFFFFu, b, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { smn[warp] = a; smx[warp] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < NWARP; ++w) { a = fminf(a, smn[w]); b = fmaxf(b, smx[w]); }
+        a = fminf(a, smn[0]);
+        b = fmaxf(b, smx[0]);
+        atomic_min_float(range_acc + 2 * j, a);
+        atomic_max_float(range_acc + 2 * j + 1, b);
+    }
+}
+
+// FP32 projections (k x P) to 8-bit codes with the range (lo, hi) pairs.
+__global__ void __launch_bounds__(TPB)
+k_f32_to_u8(const float* __restrict__ proj, int k, long long P, int vec, const float* __restrict__ range,
+            uint8_t* __restrict__ out)
+{
+    const int j = blockIdx.y;
+    const float lo = range[2 * j];
+    const float sc = code_scale(lo, range[2 * j + 1]);
+    const float* src = proj + static_cast<long long>(j) * P;
+    uint8_t* dst = out + static_cast<long long>(j) * P;
+    const long long stride = static_cast<long long>(gridDim.x) * TPB;
+    const long long start = static_cast<long long>(blockIdx.x) * TPB + threadIdx.x;
+    long long done = 0;
+    if (vec) {
+        const long long n4 = P / 4;
+        for (long long g = start; g < n4; g += stride) {
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(src) + g);
+            const uint32_t c = to_code(v.x, lo, sc) | (to_code(v.y, lo, sc) << 8) |
+                               (to_code(v.z, lo, sc) << 16) | (to_code(v.w, lo, sc) << 24);
+            __stcs(reinterpret_cast<unsigned int*>(dst) + g, c);
+        }
+        done = n4 * 4;
+    }
+    for (long long p = done + start; p < P; p += stride) dst[p] = static_cast<uint8_t>(to_code(src[p], lo, sc));
+}
+
+template <int KV, bool F32, bool U8, bool RNG>
+cudaError_t run_v8(const uint16_t* cube, int B, long long P, const DevModel* dm, int j0,
+                   const float* u8_range, float* out_f32, uint8_t* out_u8, float* range_acc,
+                   int num_sms, cudaStream_t s)
+{
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project_v8<KV, F32, U8, RNG>, TPB, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long ngroups = P / PX;
+    long long grid = (ngroups + TPB - 1) / TPB;
+    const long long cap = static_cast<long long>(num_sms) * per_sm;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    k_project_v8<KV, F32, U8, RNG><<<static_cast<unsigned>(grid), TPB, 0, s>>>(cube, B, P, dm, j0, u8_range,
+                                                                           out_f32, out_u8, range_acc);
+    return cudaGetLastError();
+}
+
+template <bool F32, bool U8, bool RNG>
+cudaError_t run_chunk(const uint16_t* cube, int B, long long P, const DevModel* dm, int j0, int kc,
+                      const float* u8_range, float* out_f32, uint8_t* out_u8, float* range_acc,
+                      bool vec, int num_sms, cudaStream_t s)
+{
+    long long p_tail = 0;
+    if (vec) {
+        cudaError_t e = cudaSuccess;
+        switch (kc) {
+            case 1: e = run_v8<1, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s); break;
+            case 2: e = run_v8<2, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s); break;
+            case 3: e = run_v8<3, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s); break;
+            case 4: e = run_v8<4, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s); break;
+            case 5: e = run_v8<5, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s); break;
+            case 6: e = run_v8<6, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s); break;
+            case 7: e = run_v8<7, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s); break;
+            default: e = run_v8<8, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s); break;
+        }
+        if (e != cudaSuccess) return e;
+        p_tail = (P / PX) * PX;
+        if (p_tail == P) return cudaSuccess;
+    }
+    long long n = P - p_tail;
+    long long grid = (n + TPB - 1) / TPB;
+    const long long cap = static_cast<long long>(num_sms) * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    k_project_s<F32, U8, RNG><<<static_cast<unsigned>(grid), TPB, 0, s>>>(cube, B, P, p_tail, dm, j0, kc, u8_range,
+                                                                     out_f32, out_u8, range_acc);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_range_init(float* range, int k, cudaStream_t s)
+{
+    k_range_init<<<1, 64, 0, s>>>(range, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_range(const uint16_t* cube, int B, long long P, const uint8_t* labels, int K,
+                               DevModel* dm, int nvec, int num_sms, cudaStream_t s)
+{
+    const long long tiles = (P + TPB * 16 - 1) / (TPB * 16);
+    long long grid = static_cast<long long>(num_sms) * 4;
+    if (grid > tiles) grid = tiles;
+    if (grid < 1) grid = 1;
+    const int vec = (reinterpret_cast<uintptr_t>(labels) % 16 == 0) ? 1 : 0;
+    for (int j0 = 0; j0 < nvec; j0 += KCH) {
+        const int kc = (nvec - j0) < KCH ? (nvec - j0) : KCH;
+        k_train_range<<<static_cast<unsigned>(grid), TPB, 0, s>>>(cube, B, P, labels, K, vec, dm, j0, kc);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_project(const uint16_t* cube, int B, long long P, const DevModel* dm, int k,
+                           float* out_f32, uint8_t* out_u8, const float* u8_range, float* range_acc,
+                           int num_sms, cudaStream_t s)
+{
+    const bool aligned = (P % PX == 0) && (reinterpret_cast<uintptr_t>(cube) % 16 == 0) &&
+                         (!out_f32 || reinterpret_cast<uintptr_t>(out_f32) % 16 == 0) &&
+                         (!out_u8 || reinterpret_cast<uintptr_t>(out_u8) % 8 == 0);
+    const bool f32 = out_f32 != nullptr, u8 = out_u8 != nullptr, rng = range_acc != nullptr;
+    for (int j0 = 0; j0 < k; j0 += KCH) {
+        const int kc = (k - j0) < KCH ? (k - j0) : KCH;
+        cudaError_t e;
+        if (f32 && !u8 && !rng)
+            e = run_chunk<true, false, false>(cube, B, P, dm, j0, kc, u8_range, out_f32, out_u8, range_acc, aligned, num_sms, s);
+        else if (f32 && !u8 && rng)
+            e = run_chunk<true, false, true>(cube, B, P, dm, j0, kc, u8_range, out_f32, out_u8, range_acc, aligned, num_sms, s);
+        else if (!f32 && !u8 && rng)
+            e = run_chunk<false, false, true>(cube, B, P, dm, j0, kc, u8_range, out_f32, out_u8, range_acc, aligned, num_sms, s);
+        else if (!f32 && u8 && !rng)
+            e = run_chunk<false, true, false>(cube, B, P, dm, j0, kc, u8_range, out_f32, out_u8, range_acc, aligned, num_sms, s);
+        else
+            return cudaErrorInvalidValue;
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_f32_range(const float* proj, int k, long long P, const DevModel*, float* range_acc,
+                             int num_sms, cudaStream_t s)
+{
+    const int vec = (reinterpret_cast<uintptr_t>(proj) % 16 == 0 && P % 4 == 0) ? 1 : 0;
+    long long gx = (P / 4 + TPB - 1) / TPB;
+    const long long cap = static_cast<long long>(num_sms) * 8;
+    if (gx > cap) gx = cap;
+    if (gx < 1) gx = 1;
+    k_f32_range<<<dim3(static_cast<unsigned>(gx), k), TPB, 0, s>>>(proj, k, P, vec, range_acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_u8(const float* proj, int k, long long P, const DevModel*, const float* range,
+                             uint8_t* out, int num_sms, cudaStream_t s)
+{
+    const int vec = (reinterpret_cast<uintptr_t>(proj) % 16 == 0 && reinterpret_cast<uintptr_t>(out) % 4 == 0 &&
+                     P % 4 == 0) ? 1 : 0;
+    long long gx = (P / 4 + TPB - 1) / TPB;
+    const long long cap = static_cast<long long>(num_sms) * 8;
+    if (gx > cap) gx = cap;
+    if (gx < 1) gx = 1;
+    k_f32_to_u8<<<dim3(static_cast<unsigned>(gx), k), TPB, 0, s>>>(proj, k, P, vec, range, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cva

@@ -1,0 +1,308 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (Section 2 readings, stated once here):
+  * class counts and exact sums: bit-exact;
+  * Sw, Sb, class means: relative 1e-10 of the largest entry (the GPU forms
+    them from exact integer moments, the oracle by two FP64 passes);
+  * eigenvalues lambda_j, j < K-1: relative 1e-6;
+  * canonical vectors v_j, j < K-1: ||v - v_ref||_Sw <= 1e-5 after the sign
+    convention (both sides scale V^T Sw V = I);
+  * vectors beyond K-1 (eigenvalue 0, not unique): V^T Sw V = I to 1e-6 and
+    ||Sb v|| <= 1e-6 ||Sb|| ||v||;
+  * FP32 projections: max |y - y_ref| / max |y_ref| <= 1e-4 per variate;
+  * 8-bit images: within one level on >= 99.9 % of pixels.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import make_workload, named_workload
+
+pytestmark = pytest.mark.gpu
+
+cva = pytest.importorskip("paper_1612_06457_gb300")
+
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+def _skip_without_gpu():
+    if DEV is None:
+        pytest.skip("no CUDA device")
+
+
+def _to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _gpu_fit(w, nvec=None, cube=None, labels=None):
+    cube = _to_dev(w.cube) if cube is None else cube
+    labels = _to_dev(w.labels) if labels is None else labels
+    m = cva.Model(w.B, w.K)
+    if nvec is not None:
+        cva.cva_set_variates(m, nvec)
+    cva.cva_fit(cube, labels, w.K, m)
+    assert cva.cva_status(m) == cva.CVA_OK
+    lam, V, mean, rng = cva.cva_model_get(m)
+    n, mc, Sw, Sb = cva.cva_model_get_scatter(m)
+    return m, cube, labels, dict(lam=lam, V=V, mu=mean, train_range=rng, n=n, mu_c=mc, Sw=Sw, Sb=Sb)
+
+
+def _check_fit(g, ref, K, B, nvec):
+    np.testing.assert_array_equal(g["n"], ref["n"])
+    for key in ("Sw", "Sb", "mu_c", "mu"):
+        scale = np.abs(ref[key]).max()
+        assert np.abs(g[key] - ref[key]).max() <= 1e-10 * scale, key
+    r = min(K - 1, B)
+    rel = np.abs(g["lam"][:r] - ref["lam"][:r]) / ref["lam"][:r]
+    assert rel.max() <= 1e-6, rel
+    Sw = ref["Sw"]
+    for j in range(min(r, nvec)):
+        d = g["V"][:, j] - ref["V"][:, j]
+        assert np.sqrt(d @ Sw @ d) <= 1e-5, (j, np.sqrt(d @ Sw @ d))
+    Vg = g["V"][:, :nvec]
+    np.testing.assert_allclose(Vg.T @ Sw @ Vg, np.eye(nvec), atol=1e-6)
+    nb = np.linalg.norm(ref["Sb"])
+    for j in range(r, nvec):
+        v = g["V"][:, j]
+        assert np.linalg.norm(ref["Sb"] @ v) <= 1e-6 * nb * np.linalg.norm(v)
+        assert g["lam"][j] == 0.0
+
+
+def _normwise(y, yref):
+    return (np.abs(y - yref).max(axis=1) / np.abs(yref).max(axis=1)).max()
+
+
+def _u8_ok(u, uref):
+    d = np.abs(u.astype(np.int32) - uref.astype(np.int32))
+    return (d <= 1).mean()
+
+
+CASES = [
+    # seed, B, H, W, K, n per class, k
+    (101, 16, 200, 264, 3, (2000, 1500, 1200), 2),
+    (102, 23, 257, 301, 4, (3000, 2000, 1500, 900), 3),   # ragged: P not a multiple of 8
+    (103, 12, 128, 128, 6, (800, 700, 600, 500, 400, 300), 5),
+    (104, 1, 64, 96, 2, (500, 400), 1),
+    (105, 2, 64, 64, 3, (300, 300, 300), 2),
+    (106, 3, 40, 33, 2, (200, 150), 1),
+    (107, 32, 96, 128, 5, (900, 800, 700, 600, 500), 4),
+    (108, 20, 1, 4096, 3, (300, 200, 100), 2),            # a single row
+    (109, 8, 4096, 1, 2, (300, 200), 1),                  # a single column
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"B{c[1]}_{c[2]}x{c[3]}_K{c[4]}" for c in CASES])
+def test_fit_project_parity(case):
+    _skip_without_gpu()
+    seed, B, H, W, K, n, k = case
+    w = make_workload(seed, B, H, W, K, n, k, separation=(1.0, 4.0), both=K >= 4)
+    ref = oracle.fit(w.cube, w.labels, w.K)
+    m, cube, labels, g = _gpu_fit(w)
+    _check_fit(g, ref, K, B, B)
+
+    # FP32 projection and its global range
+    P = w.P
+    y = torch.empty((k, H, W), dtype=torch.float32, device=DEV)
+    rg = torch.empty(2 * k, dtype=torch.float32, device=DEV)
+    cva.cva_project(cube, m, k, out_f32=y, range_out=rg)
+    yg = y.cpu().numpy().reshape(k, P)
+    # compare against the oracle projection with the GPU's own vectors (pure
+    # projection parity) and with the oracle's vectors (end-to-end parity)
+    y_own = oracle.project(w.cube, g["V"], g["mu"], k)
+    assert _normwise(yg, y_own) <= 1e-4
+    y_ref = oracle.project(w.cube, ref["V"], ref["mu"], k)
+    r = min(K - 1, B)
+    assert _normwise(yg[:r], y_ref[:r]) <= 1e-4
+    rgn = rg.cpu().numpy()
+    np.testing.assert_array_equal(rgn[0::2], yg.min(axis=1))
+    np.testing.assert_array_equal(rgn[1::2], yg.max(axis=1))
+
+    # training range: same FP32 arithmetic on the training pixels
+    lab = w.labels.reshape(-1) > 0
+    tr = g["train_range"][: 2 * k]
+    np.testing.assert_array_equal(tr[0::2], yg[:, lab].min(axis=1))
+    np.testing.assert_array_equal(tr[1::2], yg[:, lab].max(axis=1))
+
+    # 8-bit images, every route and mode, against the oracle's images
+    u_glob_ref = oracle.to_u8(y_own, oracle.range_global(y_own))
+    u_tr_ref = oracle.to_u8(y_own, oracle.range_training(y_own, w.labels))
+    out = torch.empty((k, H, W), dtype=torch.uint8, device=DEV)
+    for mode, uref in ((cva.CVA_RANGE_TRAINING, u_tr_ref), (cva.CVA_RANGE_GLOBAL, u_glob_ref)):
+        out.fill_(7)
+        cva.cva_project_u8(cube, m, k, mode, out)
+        fused = out.cpu().numpy().reshape(k, P)
+        assert _u8_ok(fused, uref) >= 0.999
+        out.fill_(7)
+        cva.cva_to_u8(y, mode, out, m=m)
+        two = out.cpu().numpy().reshape(k, P)
+        np.testing.assert_array_equal(two, fused)
+    # training extremes land on 0 and 255
+    out.fill_(7)
+    cva.cva_project_u8(cube, m, k, cva.CVA_RANGE_TRAINING, out)
+    u = out.cpu().numpy().reshape(k, P)
+    assert (u[:, lab].min(axis=1) == 0).all() and (u[:, lab].max(axis=1) == 255).all()
+    # a caller-given range
+    given = torch.tensor(np.stack([yg.min(axis=1) * 0.5, yg.max(axis=1) * 0.5], 1).reshape(-1), device=DEV)
+    out.fill_(7)
+    cva.cva_project_u8(cube, m, k, cva.CVA_RANGE_GIVEN, out, range=given)
+    ug = out.cpu().numpy().reshape(k, P)
+    uref = oracle.to_u8(y_own, given.cpu().numpy().astype(np.float64))
+    assert _u8_ok(ug, uref) >= 0.999
+    m.close()
+
+
+def test_completed_basis_and_nvec():
+    """Vectors beyond K-1 complete an Sw-orthonormal basis of the eigenvalue-0
+    space; cva_set_variates limits what a fit forms and what may be projected."""
+    _skip_without_gpu()
+    w = make_workload(111, 10, 96, 96, 3, (600, 500, 400), 2, separation=(1.0, 3.0))
+    ref = oracle.fit(w.cube, w.labels, w.K)
+    for nvec in (1, 2, 5, 10):
+        m, cube, labels, g = _gpu_fit(w, nvec=nvec)
+        _check_fit(g, ref, w.K, w.B, nvec)
+        assert np.all(g["V"][:, nvec:] == 0)
+        if nvec < w.B:
+            y = torch.empty((nvec + 1, w.H, w.W), dtype=torch.float32, device=DEV)
+            with pytest.raises(cva.CvaError) as e:
+                cva.cva_project(cube, m, nvec + 1, out_f32=y)
+            assert e.value.code == cva.CVA_ERR_INVALID_ARG
+        m.close()
+
+
+def test_unaligned_cube_and_labels():
+    """Buffers that are only 2-byte (cube) / 1-byte (labels) aligned take the
+    scalar paths and give the same results."""
+    _skip_without_gpu()
+    w = make_workload(112, 9, 120, 120, 3, (500, 400, 300), 2, separation=(1.0, 3.0))
+    base_c = torch.empty(w.cube.size + 8, dtype=torch.uint16, device=DEV)
+    cube = base_c[1:1 + w.cube.size].view(w.cube.shape)
+    cube.copy_(_to_dev(w.cube))
+    base_l = torch.empty(w.labels.size + 16, dtype=torch.uint8, device=DEV)
+    labels = base_l[3:3 + w.labels.size].view(w.labels.shape)
+    labels.copy_(_to_dev(w.labels))
+    m1, c1, l1, g1 = _gpu_fit(w)
+    m2, c2, l2, g2 = _gpu_fit(w, cube=cube, labels=labels)
+    for key in ("lam", "V", "Sw", "Sb", "train_range"):
+        np.testing.assert_array_equal(g1[key], g2[key])
+    o1 = torch.empty((2, w.H, w.W), dtype=torch.uint8, device=DEV)
+    o2 = torch.empty((2, w.H, w.W), dtype=torch.uint8, device=DEV)
+    cva.cva_project_u8(c1, m1, 2, cva.CVA_RANGE_TRAINING, o1)
+    cva.cva_project_u8(cube, m2, 2, cva.CVA_RANGE_TRAINING, o2)
+    assert torch.equal(o1, o2)
+    m1.close()
+    m2.close()
+
+
+def test_fit_is_deterministic():
+    """Exact integer moments make repeated fits bit-identical, although the
+    thread blocks merge their sums in arbitrary order."""
+    _skip_without_gpu()
+    w = make_workload(113, 23, 512, 512, 4, (5000, 4000, 3000, 2000), 3, separation=(1.0, 4.0))
+    m, cube, labels, g = _gpu_fit(w)
+    for _ in range(3):
+        cva.cva_fit(cube, labels, w.K, m)
+        lam, V, mu, rng = cva.cva_model_get(m)
+        np.testing.assert_array_equal(lam, g["lam"])
+        np.testing.assert_array_equal(V, g["V"])
+        np.testing.assert_array_equal(rng, g["train_range"])
+    m.close()
+
+
+def test_device_errors_are_reported():
+    _skip_without_gpu()
+    w = make_workload(114, 6, 64, 64, 3, (300, 300, 300), 2)
+    cube = _to_dev(w.cube)
+    out = torch.full((2, 64, 64), 7, dtype=torch.uint8, device=DEV)
+
+    def fit(c, lab):
+        m = cva.Model(w.B, w.K)
+        cva.cva_fit(c, _to_dev(lab), w.K, m)
+        return m
+
+    lab = w.labels.copy()
+    lab[lab == 2] = 0
+    m = fit(cube, lab)
+    assert cva.cva_status(m) == cva.CVA_ERR_EMPTY_CLASS
+    cva.cva_project_u8(cube, m, 2, cva.CVA_RANGE_TRAINING, out)
+    assert int(out.max()) == 7 and int(out.min()) == 7  # outputs untouched
+    with pytest.raises(cva.CvaError):
+        cva.cva_model_get(m)
+    m.close()
+
+    lab = w.labels.copy()
+    lab[5, 5] = 9
+    m = fit(cube, lab)
+    assert cva.cva_status(m) == cva.CVA_ERR_LABEL_RANGE
+    m.close()
+
+    dead = w.cube.copy()
+    dead[3] = 2000
+    m = fit(_to_dev(dead), w.labels)
+    assert cva.cva_status(m) == cva.CVA_ERR_NOT_SPD
+    m.close()
+
+    # the model recovers with a good fit afterwards
+    m = fit(cube, w.labels)
+    assert cva.cva_status(m) == cva.CVA_OK
+    m.close()
+
+
+def test_argument_errors_are_immediate():
+    _skip_without_gpu()
+    w = make_workload(115, 5, 32, 32, 2, (100, 100), 1)
+    cube = _to_dev(w.cube)
+    labels = _to_dev(w.labels)
+    m = cva.Model(w.B, w.K)
+    lib = cva.load()
+    import ctypes
+
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    host = np.zeros(w.cube.size, np.uint16)
+    assert lib.cva_fit(ctypes.c_void_p(host.ctypes.data), w.B, 32, 32, ctypes.c_void_p(labels.data_ptr()), 2,
+                       m.handle, s) == cva.CVA_ERR_INVALID_ARG  # pageable host memory
+    assert lib.cva_fit(ctypes.c_void_p(cube.data_ptr()), w.B + 1, 32, 32, ctypes.c_void_p(labels.data_ptr()), 2,
+                       m.handle, s) == cva.CVA_ERR_INVALID_ARG  # band count mismatch
+    assert lib.cva_fit(ctypes.c_void_p(cube.data_ptr()), w.B, 0, 32, ctypes.c_void_p(labels.data_ptr()), 2,
+                       m.handle, s) == cva.CVA_ERR_INVALID_ARG
+    assert lib.cva_project_u8(ctypes.c_void_p(cube.data_ptr()), w.B, 32, 32, m.handle, 1, 5, None,
+                              ctypes.c_void_p(labels.data_ptr()), s) == cva.CVA_ERR_INVALID_ARG  # bad mode
+    h = ctypes.c_void_p()
+    assert lib.cva_model_create(33, 2, ctypes.byref(h)) == cva.CVA_ERR_INVALID_ARG
+    assert lib.cva_model_create(4, 1, ctypes.byref(h)) == cva.CVA_ERR_INVALID_ARG
+    assert lib.cva_model_create(4, 17, ctypes.byref(h)) == cva.CVA_ERR_INVALID_ARG
+    with pytest.raises(cva.CvaError) as e:
+        cva.cva_model_get(m)
+    assert e.value.code == cva.CVA_ERR_NOT_FITTED
+    m.close()
+
+
+def test_max_bands_and_classes():
+    """B = 32 bands and K = 16 classes, the ABI's limits."""
+    _skip_without_gpu()
+    w = make_workload(116, 32, 160, 160, 16, tuple([150] * 16), 15, separation=(1.0, 4.0))
+    ref = oracle.fit(w.cube, w.labels, w.K)
+    m, cube, labels, g = _gpu_fit(w)
+    _check_fit(g, ref, w.K, w.B, w.B)
+    m.close()
+
+
+def test_full_size_23_band_4096x4096_cube():
+    """The 23-band 4096 x 4096 cube, 4 classes of 50 000 training pixels,
+    3 variates, exactly as the benchmark runs it (fit, then fused projection
+    with the training range), compared in full with the oracle."""
+    _skip_without_gpu()
+    w = named_workload("cube23b_4096x4096_K4")
+    ref = oracle.fit(w.cube, w.labels, w.K)
+    m, cube, labels, g = _gpu_fit(w, nvec=w.k)
+    _check_fit(g, ref, w.K, w.B, w.k)
+    out = torch.empty((w.k, w.H, w.W), dtype=torch.uint8, device=DEV)
+    cva.cva_project_u8(cube, m, w.k, cva.CVA_RANGE_TRAINING, out)
+    u = out.cpu().numpy().reshape(w.k, -1)
+    y_ref = oracle.project(w.cube, ref["V"], ref["mu"], w.k)
+    uref = oracle.to_u8(y_ref, oracle.range_training(y_ref, w.labels))
+    assert _u8_ok(u, uref) >= 0.999
+    y = torch.empty((w.k, w.H, w.W), dtype=torch.float32, device=DEV)
+    cva.cva_project(cube, m, w.k, out_f32=y)
+    assert _normwise(y.cpu().numpy().reshape(w.k, -1), y_ref) <= 1e-4
+    m.close()
