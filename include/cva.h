@@ -52,6 +52,7 @@ extern "C" {
 #define CVA_ERR_CUDA (-6)           /* a CUDA runtime call failed */
 #define CVA_ERR_LABEL_RANGE (-7)    /* a label is above K */
 #define CVA_ERR_NOT_FITTED (-8)     /* the model has not been fitted */
+#define CVA_ERR_CAPACITY (-9)       /* more training pixels than the model can hold */
 
 /* Which range maps a projection onto 0..255 (Section 2 gives the first two). */
 typedef enum {
@@ -75,10 +76,19 @@ typedef enum {
 typedef struct cva_model cva_model;
 
 /* Create a model for B bands and K classes on the current CUDA device.  Owns
- * a small device block (a few hundred KB) until cva_model_destroy.  *out is
- * set to NULL on error.  Not stream-ordered: allocates with cudaMalloc, so
- * call it outside stream capture. */
+ * until cva_model_destroy: a device block of about 150 KB, a per-tile
+ * workspace of 0.5 MB per class, and the gathered training matrix of
+ * 2 ((B + 8) & ~7) bytes per training pixel with room for
+ * CVA_DEFAULT_TRAIN_CAPACITY pixels (see cva_model_reserve).  *out is set to
+ * NULL on error.  Not stream-ordered: allocates with cudaMalloc, so call it
+ * outside stream capture. */
+#define CVA_DEFAULT_TRAIN_CAPACITY (1 << 22)
 int cva_model_create(int B, int K, cva_model** out);
+
+/* Make room for up to `max_train` labelled training pixels per fit (a fit
+ * with more sets CVA_ERR_CAPACITY in the device status).  Synchronizes the
+ * device and reallocates; call it outside stream capture. */
+int cva_model_reserve(cva_model* m, int64_t max_train);
 
 /* Free the model (synchronizes the device first).  NULL is a no-op. */
 void cva_model_destroy(cva_model* m);
@@ -103,8 +113,12 @@ int cva_set_variates(cva_model* m, int nvec);
  * component of each positive (lowest band on a tie), the training mean, and
  * the training-score range of each variate.  Sw and Sb are unnormalised
  * sums of squares and cross-products.  Forms the number of vectors set by
- * cva_set_variates.  Only kernel launches and one memset on `stream`: no
- * host synchronization and no allocation. */
+ * cva_set_variates.  Only kernel launches on `stream`: no host
+ * synchronization and no allocation.  The labelled pixels are counted,
+ * gathered class by class into the model's training matrix, and their exact
+ * integer moments accumulated; errors (a label above K, an empty class, more
+ * training pixels than the matrix holds, Sw not positive definite) go to the
+ * device status. */
 int cva_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, int K,
             cva_model* m, void* stream);
 

@@ -25,6 +25,7 @@ CVA_ERR_TIMEOUT = -5
 CVA_ERR_CUDA = -6
 CVA_ERR_LABEL_RANGE = -7
 CVA_ERR_NOT_FITTED = -8
+CVA_ERR_CAPACITY = -9
 
 CVA_RANGE_GLOBAL = 0
 CVA_RANGE_TRAINING = 1
@@ -42,6 +43,7 @@ _I = ctypes.c_int
 SIGNATURES = {
     "cva_model_create": (_I, [_I, _I, ctypes.POINTER(_P)]),
     "cva_model_destroy": (None, [_P]),
+    "cva_model_reserve": (_I, [_P, ctypes.c_int64]),
     "cva_set_precision": (_I, [_P, _I]),
     "cva_set_variates": (_I, [_P, _I]),
     "cva_fit": (_I, [_P, _I, _I, _I, _P, _I, _P, _P]),
@@ -143,6 +145,10 @@ def cva_model_create(B: int, K: int) -> Model:
 
 def cva_model_destroy(m: Model) -> None:
     m.close()
+
+
+def cva_model_reserve(m: Model, max_train: int) -> None:
+    _check(load().cva_model_reserve(m.handle, max_train), "cva_model_reserve")
 
 
 def cva_set_precision(m: Model, mode: int) -> None:

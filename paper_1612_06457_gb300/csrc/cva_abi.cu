@@ -17,6 +17,9 @@ struct cva_model {
     int nvec;
     int precision;
     cva::DevModel* dm;
+    unsigned int* tiles; // per-tile class counts, then first rows (MAX_TILES x (K + 1))
+    uint16_t* xtr;       // gathered training matrix, cap rows of xtr_row(B)
+    long long cap;       // rows of `xtr`
 };
 
 namespace {
@@ -76,6 +79,7 @@ const char* cva_strerror(int code)
         case CVA_ERR_CUDA: return "CUDA runtime error";
         case CVA_ERR_LABEL_RANGE: return "a label is above the class count";
         case CVA_ERR_NOT_FITTED: return "model not fitted";
+        case CVA_ERR_CAPACITY: return "more training pixels than the model's index buffer holds";
         default: return "unknown error";
     }
 }
@@ -89,14 +93,23 @@ int cva_model_create(int B, int K, cva_model** out)
     if (cudaGetDevice(&dev) != cudaSuccess) return CVA_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CVA_ERR_CUDA;
     DevModel* dm = nullptr;
+    unsigned int* tiles = nullptr;
+    uint16_t* xtr = nullptr;
+    const size_t cap = CVA_DEFAULT_TRAIN_CAPACITY;
     if (cudaMalloc(&dm, sizeof(DevModel)) != cudaSuccess) return CVA_ERR_CUDA;
-    if (cudaMemset(dm, 0, sizeof(DevModel)) != cudaSuccess) {
+    if (cudaMalloc(&tiles, sizeof(unsigned int) * static_cast<size_t>(cva::MAX_TILES) * (K + 1)) != cudaSuccess ||
+        cudaMalloc(&xtr, sizeof(uint16_t) * cap * cva::xtr_row(B)) != cudaSuccess ||
+        cudaMemset(dm, 0, sizeof(DevModel)) != cudaSuccess) {
         cudaFree(dm);
+        cudaFree(tiles);
+        cudaFree(xtr);
         return CVA_ERR_CUDA;
     }
     cva_model* m = new (std::nothrow) cva_model;
     if (!m) {
         cudaFree(dm);
+        cudaFree(tiles);
+        cudaFree(xtr);
         return CVA_ERR_INVALID_ARG;
     }
     m->B = B;
@@ -106,7 +119,24 @@ int cva_model_create(int B, int K, cva_model** out)
     m->nvec = B;
     m->precision = CVA_PRECISION_EXACT;
     m->dm = dm;
+    m->tiles = tiles;
+    m->xtr = xtr;
+    m->cap = static_cast<long long>(cap);
     *out = m;
+    return CVA_OK;
+}
+
+int cva_model_reserve(cva_model* m, int64_t max_train)
+{
+    if (!m || max_train < 1 || max_train >= (1LL << 31)) return CVA_ERR_INVALID_ARG;
+    if (max_train <= m->cap) return CVA_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return CVA_ERR_CUDA;
+    uint16_t* xtr = nullptr;
+    if (cudaMalloc(&xtr, sizeof(uint16_t) * static_cast<size_t>(max_train) * cva::xtr_row(m->B)) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    cudaFree(m->xtr);
+    m->xtr = xtr;
+    m->cap = max_train;
     return CVA_OK;
 }
 
@@ -115,6 +145,8 @@ void cva_model_destroy(cva_model* m)
     if (!m) return;
     cudaDeviceSynchronize();
     cudaFree(m->dm);
+    cudaFree(m->tiles);
+    cudaFree(m->xtr);
     delete m;
 }
 
@@ -140,10 +172,9 @@ int cva_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, in
     if (!device_visible(cube) || !device_visible(labels)) return CVA_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long P = static_cast<long long>(H) * W;
-    cudaError_t e = cudaMemsetAsync(m->dm, 0, offsetof(DevModel, n), s);
-    if (e == cudaSuccess) e = cva::launch_fit_moments(cube, B, P, labels, K, m->dm, m->num_sms, s);
+    cudaError_t e = cva::launch_fit_moments(cube, B, P, labels, K, m->dm, m->xtr, m->tiles, m->cap, m->num_sms, s);
     if (e == cudaSuccess) e = cva::launch_fit_finalize(m->dm, B, K, m->nvec, s);
-    if (e == cudaSuccess) e = cva::launch_train_range(cube, B, P, labels, K, m->dm, m->nvec, m->num_sms, s);
+    if (e == cudaSuccess) e = cva::launch_train_range(B, K, m->xtr, m->dm, m->nvec, m->num_sms, s);
     return from_cuda(e);
 }
 
@@ -185,6 +216,9 @@ int cva_model_get_scatter(cva_model* m, int64_t* counts, double* class_means, do
     if (!fitted) return CVA_ERR_NOT_FITTED;
     const int B = m->B, K = m->K;
     const DevModel* dm = m->dm;
+    if (Sb && (cva::launch_scatter_sb(m->dm, B, K, static_cast<cudaStream_t>(stream)) != cudaSuccess ||
+               cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess))
+        return CVA_ERR_CUDA;
     if (counts && cudaMemcpy(counts, dm->n, sizeof(int64_t) * K, cudaMemcpyDeviceToHost) != cudaSuccess)
         return CVA_ERR_CUDA;
     if (class_means && cudaMemcpy2D(class_means, sizeof(double) * B, dm->mu_c, sizeof(double) * cva::MAXB,

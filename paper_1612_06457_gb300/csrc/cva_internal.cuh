@@ -17,6 +17,9 @@ constexpr int MAXK = CVA_MAX_CLASSES;                   // 16 classes
 constexpr int MAXBA = ((MAXB + 1 + 3) / 4) * 4;         // augmented bands, padded to 4: 36
 constexpr int MAXNB = MAXBA / 4;                        // 4-band blocks: 9
 constexpr int MAXBLK = MAXNB * (MAXNB + 1) / 2;         // upper-triangle block pairs: 45
+constexpr int LABEL_TILE = 16384;                       // labels per CTA of the label passes
+constexpr long long MAX_PIXELS = 1LL << 31;             // H W limit of the ABI
+constexpr int MAX_TILES = static_cast<int>(MAX_PIXELS / LABEL_TILE);  // 131072
 
 // Pivot test of the Cholesky factorization: Sw is "not positive definite"
 // when a pivot is not above this multiple of its own diagonal entry.
@@ -52,21 +55,23 @@ __host__ __device__ inline int blk_index(int bi, int bj, int nb)
 // Device-resident model.  One per cva_model; written by the fit kernels and
 // read by the projection kernels.  All matrices are [row][column].
 struct DevModel {
-    // ---- fit workspace: zeroed at the start of every fit -------------------
+    // ---- fit workspace: reset by the label scan of every fit ---------------
     // Exact integer moments of the augmented training vectors (x, 1) per
     // class: block pair (bi, bj), slot 4a + b holds sum x'_{4bi+a} x'_{4bj+b}.
     unsigned long long mom[MAXK][MAXBLK][16];
-    int status;   // CVA_OK or the first device-side error
+    int status;   // CVA_OK or the first device-side error of the current fit
     int fitted;   // 1 once a fit finished without error
     int r;        // eigenpairs taken from the reduced K x K problem
     int nvec;     // canonical vectors formed (columns of V)
+    unsigned int cls_count[MAXK];   // training pixels per class
 
     // ---- fit results --------------------------------------------------------
     long long n[MAXK];          // training pixels per class
     double mu_c[MAXK][MAXB];    // class means
     double mu[MAXB];            // mean of all training pixels
     double Sw[MAXB][MAXB];      // within-class scatter
-    double Sb[MAXB][MAXB];      // between-class scatter
+    double Sb[MAXB][MAXB];      // between-class scatter (formed on request from Mb)
+    double Mb[MAXB][MAXK];      // sqrt(n_c) (mu_c - mu): Sb = Mb Mb^T
     double L[MAXB][MAXB];       // lower Cholesky factor of Sw
     double Linvd[MAXB];         // 1 / L[i][i]
     double U[MAXB][MAXB];       // whitened eigenvectors, U = L^T V
@@ -88,11 +93,24 @@ struct DevModel {
 // launchers (each defined in the translation unit that holds its kernel)
 // -------------------------------------------------------------------------
 
+// Row length (uint16 entries) of the gathered training matrix: the B band
+// values, a 1, and zeros up to a multiple of 8 (16-byte rows).
+__host__ __device__ inline int xtr_row(int B)
+{
+    return (B + 1 + 7) & ~7;
+}
+
+// Training-pixel passes: per-tile class counts (`tiles`: ceil(P / LABEL_TILE)
+// rows of K + 1 words), their prefix sums, the gather of every training
+// pixel's bands into the class-major matrix `xtr` (`cap` rows of
+// xtr_row(B)), then the exact moments from it.
 cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const uint8_t* labels,
-                               int K, DevModel* dm, int num_sms, cudaStream_t s);
+                               int K, DevModel* dm, uint16_t* xtr, unsigned int* tiles, long long cap,
+                               int num_sms, cudaStream_t s);
 cudaError_t launch_fit_finalize(DevModel* dm, int B, int K, int nvec, cudaStream_t s);
-cudaError_t launch_train_range(const uint16_t* cube, int B, long long P, const uint8_t* labels,
-                               int K, DevModel* dm, int nvec, int num_sms, cudaStream_t s);
+cudaError_t launch_train_range(int B, int K, const uint16_t* xtr, DevModel* dm, int nvec, int num_sms,
+                               cudaStream_t s);
+cudaError_t launch_scatter_sb(DevModel* dm, int B, int K, cudaStream_t s);
 cudaError_t launch_range_init(float* range, int k, cudaStream_t s);
 cudaError_t launch_project(const uint16_t* cube, int B, long long P, const DevModel* dm, int k,
                            float* out_f32, uint8_t* out_u8, const float* u8_range,

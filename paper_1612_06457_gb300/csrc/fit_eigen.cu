@@ -5,60 +5,87 @@
 // their eigenanalysis as the canonical vectors; Section 4 solves that
 // eigenanalysis with GSL's generalized symmetric-definite solver, i.e.
 //     Sb v = lambda Sw v .
-// Everything here runs in FP64 on a single CTA, so the eigensolve never
-// touches the host:
+// Everything here runs on a single CTA, so the eigensolve never touches the
+// host.  Every quantity whose rounding reaches the results is carried in
+// double-float arithmetic (dfloat.cuh, ~48-bit significands on the FP32
+// pipe): on GB300 a dependent FP64 operation costs about 64 cycles against
+// under 5 for FP32, and this kernel is one long chain of dependent steps.
+// FP64 is used only to publish the results into the model.
 //
-//  1. Sw and Sb from the exact integer moments of fit_moments.cu:
+//  1. Sw and Mb from the exact integer moments of fit_moments.cu:
 //       Sw[i][j] = sum_c (n_c M_c[i][j] - s_c[i] s_c[j]) / n_c
-//     whose numerator is an exact 128-bit integer, and Sb = Mb Mb^T with the
-//     B x K matrix Mb[:, c] = sqrt(n_c) (mu_c - mu), whose entries are
-//     exact 128-bit numerators over n_c N;
-//  2. Cholesky Sw = L L^T (right-looking), carrying Mb along as extra
-//     columns so the same elimination yields G = L^-1 Mb;
+//     whose numerators are exact 128-bit integers (the cancellation happens
+//     before any rounding), and the B x K matrix
+//       Mb[:, c] = sqrt(n_c) (mu_c - mu),  mu_c - mu = (N s_c - n_c S) / (n_c N)
+//     again from exact numerators, so that Sb = Mb Mb^T;
+//  2. right-looking Cholesky Sw = L L^T with Mb carried along as extra
+//     columns, giving G = L^-1 Mb in the same elimination (two barriers per
+//     column; the next pivot's reciprocal square root is taken by the thread
+//     that finishes that diagonal entry);
 //  3. L^-1 Sb L^-T = G G^T has rank <= K - 1 and the same non-zero
-//     eigenvalues as the K x K matrix G^T G, which is diagonalized by the
-//     cyclic Jacobi method in round-robin (parallel) order; the rotation
-//     angle is taken in FP32 and the rotation itself made orthogonal to
-//     FP64 accuracy by a Newton step on its cosine;
+//     eigenvalues as the K x K matrix T = G^T G.  T is diagonalized by the
+//     cyclic Jacobi method in FP32 (round-robin order, one warp), and the
+//     eigenvectors are then refined in double-float by two steps of the Ogita-Aishima
+//     iteration for symmetric eigendecompositions (T. Ogita, K. Aishima,
+//     "Iterative refinement for symmetric eigenvalue decomposition", Japan J.
+//     Indust. Appl. Math. 35, 2018), which restores full accuracy from the
+//     FP32 start and tolerates its loss of orthogonality;
 //  4. u_j = G w_j / sqrt(lambda_j) are the eigenvectors of G G^T with
 //     non-zero eigenvalue; the eigenvalue-0 directions (not unique) are
 //     completed by pivoted Gram-Schmidt on the unit vectors, applied twice;
-//  5. V = L^-T U (so V^T Sw V = I), the sign convention (largest-magnitude
-//     component positive, lowest band on a tie), and the FP32 coefficients
-//     used by the projection kernels.
+//  5. V = L^-T U (so V^T Sw V = I) by back substitution, the sign convention
+//     (largest-magnitude component positive, lowest band on a tie), and the
+//     FP32 coefficients used by the projection kernels.
 #include <math.h>
 
 #include "cva_internal.cuh"
+#include "dfloat.cuh"
 
 namespace cva {
 
 namespace {
 
 constexpr int TPB = 256;
-constexpr int MAX_SWEEPS = 60;
-constexpr double OFF_TOL2 = 1e-28;  // squared off-diagonal norm of the unit-norm K x K matrix
+constexpr int NWARP = TPB / 32;
+constexpr int JACOBI_SWEEPS = 40;
+constexpr int REFINE_STEPS = 2;
+constexpr int MAXTRI = MAXB * (MAXB + 1) / 2;
 
 struct FinSmem {
-    double A[MAXB][MAXB + MAXK + 1];  // [Sw | Mb] during elimination, then back-substitution work
-    double L[MAXB][MAXB + 1];
-    double G[MAXB][MAXK + 1];
-    double T[MAXK][MAXK + 1];
-    double Wv[MAXK][MAXK + 1];
-    double U[MAXB][MAXB + 1];
-    double V[MAXB][MAXB + 1];
-    double swd[MAXB];
-    double invd[MAXB];
-    double lam[MAXB];
-    double res[MAXB];
-    double q[MAXB];
-    double cvec[MAXB];
-    double rot_c[MAXK / 2], rot_s[MAXK / 2];
-    int rot_p[MAXK / 2], rot_q[MAXK / 2], rot_ok[MAXK / 2];
+    df A[MAXB][MAXB + MAXK + 1];  // [Sw | Mb] during elimination, then back-substitution work
+    df L[MAXB][MAXB + 1];
+    df G[MAXB][MAXK + 1];
+    df T[MAXK][MAXK + 1];
+    df W[MAXK][MAXK + 1];
+    df R[MAXK][MAXK + 1];
+    df TW[MAXK][MAXK + 1];
+    df S[MAXK][MAXK + 1];
+    df E[MAXK][MAXK + 1];
+    float Tf[MAXK][MAXK + 1];
+    float Wf[MAXK][MAXK + 1];
+    df U[MAXB][MAXB + 1];
+    df V[MAXB][MAXB + 1];
+    df mu[MAXB];
+    df invd[MAXB];
+    df lamk[MAXK];
+    df lam[MAXB];
+    df q[MAXB];
+    df cvec[MAXB];
+    df invn[MAXK];
+    df sqn[MAXK];
+    float swd[MAXB];
+    float res[MAXB];
+    float rc[MAXK / 2], rs[MAXK / 2];
+    int rp[MAXK / 2], rq[MAXK / 2], rok[MAXK / 2];
     int order[MAXK];
+    unsigned char rr[MAXK][MAXK];
     unsigned long long n[MAXK];
     unsigned long long tot[MAXB];
+    unsigned char tri_i[MAXTRI], tri_l[MAXTRI];
     unsigned long long N;
-    double fro;
+    df invN;
+    df rnorm;
+    float scale;     // power of two bringing T to about unit Frobenius norm
     int fail;
     int r_eff;
     int pivot;
@@ -70,32 +97,20 @@ __device__ inline unsigned long long mom_get(const DevModel* dm, const MomShape&
     return dm->mom[c][blk_index(i >> 2, j >> 2, sh.nb)][(i & 3) * 4 + (j & 3)];
 }
 
-__device__ inline double i128_to_double(__int128 v)
-{
-    const bool neg = v < 0;
-    const unsigned __int128 u = neg ? static_cast<unsigned __int128>(-v) : static_cast<unsigned __int128>(v);
-    const double d = static_cast<double>(static_cast<unsigned long long>(u >> 64)) * 18446744073709551616.0 +
-                     static_cast<double>(static_cast<unsigned long long>(u));
-    return neg ? -d : d;
-}
-
-// 1 / sqrt(d) in FP64: an FP32 estimate refined by two Newton steps on
-// f(r) = 1 / r^2 - d (each step squares the relative error: ~1e-7 -> ~1e-14
-// -> rounding level).
-__device__ inline double rsqrt_fp64(double d)
-{
-    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-    double r = static_cast<double>(rsqrtf(static_cast<float>(d)));
-    double e = fma(-d * r, r, 1.0);
-    r = fma(0.5 * r, e, r);
-    e = fma(-d * r, r, 1.0);
-    r = fma(0.5 * r, e, r);
-    return r;
-}
-
-__device__ inline double warp_sum(double v)
+__device__ inline float warp_sumf(float v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__device__ inline df shfl_xor_df(df v, int o)
+{
+    return df_make(__shfl_xor_sync(0xFFFFFFFFu, v.hi, o), __shfl_xor_sync(0xFFFFFFFFu, v.lo, o));
+}
+
+__device__ inline df warp_sum_df(df v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = df_add(v, shfl_xor_df(v, o));
     return v;
 }
 
@@ -114,9 +129,9 @@ __device__ void complete_basis(FinSmem& sm, int B, int j0, int j1)
     const int tid = threadIdx.x;
     for (int j = j0; j < j1; ++j) {
         if (tid < B) {
-            double s = 0.0;
-            for (int l = 0; l < j; ++l) s += sm.U[tid][l] * sm.U[tid][l];
-            sm.res[tid] = 1.0 - s;
+            float s = 0.0f;
+            for (int l = 0; l < j; ++l) s = fmaf(sm.U[tid][l].hi, sm.U[tid][l].hi, s);
+            sm.res[tid] = 1.0f - s;
         }
         __syncthreads();
         if (tid == 0) {
@@ -128,32 +143,31 @@ __device__ void complete_basis(FinSmem& sm, int B, int j0, int j1)
         __syncthreads();
         const int piv = sm.pivot;
         if (tid < B) {
-            double s = (tid == piv) ? 1.0 : 0.0;
-            for (int l = 0; l < j; ++l) s -= sm.U[piv][l] * sm.U[tid][l];
+            df s = df_from((tid == piv) ? 1.0f : 0.0f);
+            for (int l = 0; l < j; ++l) s = df_fms(s, sm.U[piv][l], sm.U[tid][l]);
             sm.q[tid] = s;
         }
         __syncthreads();
         if (tid < j) {
-            double s = 0.0;
-            for (int b = 0; b < B; ++b) s += sm.U[b][tid] * sm.q[b];
+            df s = df_from(0.0f);
+            for (int b = 0; b < B; ++b) s = df_fma(s, sm.U[b][tid], sm.q[b]);
             sm.cvec[tid] = s;
         }
         __syncthreads();
         if (tid < B) {
-            double s = sm.q[tid];
-            for (int l = 0; l < j; ++l) s -= sm.cvec[l] * sm.U[tid][l];
+            df s = sm.q[tid];
+            for (int l = 0; l < j; ++l) s = df_fms(s, sm.cvec[l], sm.U[tid][l]);
             sm.q[tid] = s;
         }
         __syncthreads();
         if (tid < 32) {
-            double s = 0.0;
-            for (int b = tid; b < B; b += 32) s += sm.q[b] * sm.q[b];
-            s = warp_sum(s);
-            if (tid == 0) sm.res[0] = rsqrt_fp64(s);
+            df s = df_from(0.0f);
+            for (int b = tid; b < B; b += 32) s = df_fma(s, sm.q[b], sm.q[b]);
+            s = warp_sum_df(s);
+            if (tid == 0) sm.rnorm = df_rsqrt(s);
         }
         __syncthreads();
-        const double inv = sm.res[0];
-        if (tid < B) sm.U[tid][j] = sm.q[tid] * inv;
+        if (tid < B) sm.U[tid][j] = df_mul(sm.q[tid], sm.rnorm);
         __syncthreads();
     }
 }
@@ -163,16 +177,22 @@ __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm,
     extern __shared__ __align__(16) unsigned char fin_dyn[];
     FinSmem& sm = *reinterpret_cast<FinSmem*>(fin_dyn);
     const MomShape sh = mom_shape(B);
-    const int tid = threadIdx.x;
-    if (dm->status != 0) return;  // the moments pass already failed
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (dm->status != 0) return;  // an earlier pass already failed
 
-    // ---- 1. counts, totals, Sw and Mb (exact numerators) -------------------
+    // ---- 0. counts, totals, triangle tables ---------------------------------
     if (tid < K) sm.n[tid] = mom_get(dm, sh, tid, B, B);
     if (tid < B) {
         unsigned long long t = 0;
         for (int c = 0; c < K; ++c) t += mom_get(dm, sh, c, tid, B);
         sm.tot[tid] = t;
     }
+    for (int i = warp; i < MAXB; i += NWARP)
+        for (int l = lane; l <= i; l += 32) {
+            const int q = i * (i + 1) / 2 + l;
+            sm.tri_i[q] = static_cast<unsigned char>(i);
+            sm.tri_l[q] = static_cast<unsigned char>(l);
+        }
     __syncthreads();
     if (tid == 0) {
         unsigned long long N = 0;
@@ -183,282 +203,391 @@ __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm,
         }
         sm.N = N;
         sm.fail = fail;
+        if (N) sm.invN = df_rcp(df_from_u64(N));
+    }
+    if (tid < K && sm.n[tid]) {
+        const df n = df_from_u64(sm.n[tid]);
+        sm.invn[tid] = df_rcp(n);
+        sm.sqn[tid] = df_mul(n, df_rsqrt(n));
     }
     __syncthreads();
     if (sm.fail) {
         if (tid == 0) set_status(dm, sm.fail);
         return;
     }
-    for (int e = tid; e < B * B; e += TPB) {
-        const int i = e / B, j = e - (e / B) * B;
-        if (j < i) continue;
-        double acc = 0.0;
-        for (int c = 0; c < K; ++c) {
-            const unsigned long long nc = sm.n[c];
-            const __int128 num = static_cast<__int128>(nc) * static_cast<__int128>(mom_get(dm, sh, c, i, j)) -
-                                 static_cast<__int128>(mom_get(dm, sh, c, i, B)) *
-                                     static_cast<__int128>(mom_get(dm, sh, c, j, B));
-            acc += i128_to_double(num) / static_cast<double>(nc);
-        }
-        sm.A[i][j] = acc;
-        sm.A[j][i] = acc;
-        dm->Sw[i][j] = acc;
-        dm->Sw[j][i] = acc;
-    }
-    for (int e = tid; e < B * K; e += TPB) {
-        const int b = e / K, c = e - (e / K) * K;
-        const unsigned long long nc = sm.n[c];
+
+    // ---- 1. class means, Sw and Mb from exact numerators ----------------------
+    for (int e = tid; e < K * B; e += TPB) {
+        const int c = e / B, b = e - (e / B) * B;
         const unsigned long long s = mom_get(dm, sh, c, b, B);
-        const __int128 num = static_cast<__int128>(sm.N) * static_cast<__int128>(s) -
-                             static_cast<__int128>(nc) * static_cast<__int128>(sm.tot[b]);
-        const double diff = i128_to_double(num) / (static_cast<double>(nc) * static_cast<double>(sm.N));
-        sm.A[b][B + c] = sqrt(static_cast<double>(nc)) * diff;
-        dm->mu_c[c][b] = static_cast<double>(s) / static_cast<double>(nc);
+        dm->mu_c[c][b] = df_to_double(df_mul(df_from_u64(s), sm.invn[c]));
+        const __int128 num = static_cast<__int128>(sm.N) * s - static_cast<__int128>(sm.n[c]) * sm.tot[b];
+        const df v = df_mul(df_mul(df_mul(df_from_i128(num), sm.invn[c]), sm.invN), sm.sqn[c]);
+        sm.A[b][B + c] = v;
+        dm->Mb[b][c] = df_to_double(v);
     }
-    if (tid < B) dm->mu[tid] = static_cast<double>(sm.tot[tid]) / static_cast<double>(sm.N);
+    if (tid < B) {
+        sm.mu[tid] = df_mul(df_from_u64(sm.tot[tid]), sm.invN);
+        dm->mu[tid] = df_to_double(sm.mu[tid]);
+    }
     if (tid < K) dm->n[tid] = static_cast<long long>(sm.n[tid]);
-    __syncthreads();
-    for (int e = tid; e < B * B; e += TPB) {
-        const int i = e / B, j = e - (e / B) * B;
-        double acc = 0.0;
-        for (int c = 0; c < K; ++c) acc += sm.A[i][B + c] * sm.A[j][B + c];
-        dm->Sb[i][j] = acc;
+    for (int q = tid; q < B * (B + 1) / 2; q += TPB) {
+        const int i = sm.tri_i[q], l = sm.tri_l[q];
+        df acc = df_from(0.0f);
+        for (int c = 0; c < K; ++c) {
+            const __int128 num = static_cast<__int128>(sm.n[c]) * mom_get(dm, sh, c, i, l) -
+                                 static_cast<__int128>(mom_get(dm, sh, c, i, B)) * mom_get(dm, sh, c, l, B);
+            acc = df_add(acc, df_mul(df_from_i128(num), sm.invn[c]));
+        }
+        sm.A[i][l] = acc;
+        sm.A[l][i] = acc;
+        const double d = df_to_double(acc);
+        dm->Sw[i][l] = d;
+        dm->Sw[l][i] = d;
     }
-    if (tid < B) sm.swd[tid] = sm.A[tid][tid];
-    for (int e = tid; e < MAXB * (MAXB + 1); e += TPB) (&sm.L[0][0])[e] = 0.0;
+    __syncthreads();
+    if (tid < B) sm.swd[tid] = sm.A[tid][tid].hi;
+    for (int e = tid; e < MAXB * (MAXB + 1); e += TPB) (&sm.L[0][0])[e] = df_from(0.0f);
     __syncthreads();
 
     // ---- 2. Cholesky of Sw with Mb carried along: L and G = L^-1 Mb ---------
-    for (int j = 0; j < B; ++j) {
-        if (tid == 0) {
-            const double d = sm.A[j][j];
-            if (!(d > PIVOT_REL * sm.swd[j])) {
-                sm.fail = CVA_ERR_NOT_SPD;
-            } else {
-                const double r = rsqrt_fp64(d);
-                sm.invd[j] = r;
-                sm.L[j][j] = d * r;
-            }
+    if (tid == 0) {
+        const df d = sm.A[0][0];
+        if (!(d.hi > static_cast<float>(PIVOT_REL) * sm.swd[0]) || !(d.hi > 0.0f)) {
+            sm.fail = CVA_ERR_NOT_SPD;
+        } else {
+            const df r = df_rsqrt(d);
+            sm.invd[0] = r;
+            sm.L[0][0] = df_mul(d, r);
         }
+    }
+    for (int j = 0; j < B; ++j) {
         __syncthreads();
         if (sm.fail) break;
-        const double r = sm.invd[j];
-        const double r2 = r * r;
+        // column j of L, row j of G, and the trailing update, in one phase:
+        // L[i][j] = A[i][j] r and G[j][c] = A[j][B + c] r are formed where used
+        const df r = sm.invd[j];
         const int m = B - j - 1;
-        const int na = m, nbk = K, nc = m * m, nd = m * K;
-        for (int e = tid; e < na + nbk + nc + nd; e += TPB) {
-            if (e < na) {
-                const int i = j + 1 + e;
-                sm.L[i][j] = sm.A[i][j] * r;
-            } else if (e < na + nbk) {
-                const int c = e - na;
-                sm.G[j][c] = sm.A[j][B + c] * r;
-            } else if (e < na + nbk + nc) {
-                const int q = e - na - nbk;
-                const int i = j + 1 + q / m, l = j + 1 + q % m;
-                if (l <= i) sm.A[i][l] -= sm.A[i][j] * sm.A[l][j] * r2;
+        const int ntri = m * (m + 1) / 2;
+        for (int e = tid; e < ntri + m * K + m + K; e += TPB) {
+            if (e < ntri) {
+                const int i = j + 1 + sm.tri_i[e], l = j + 1 + sm.tri_l[e];
+                const df v = df_fms(sm.A[i][l], df_mul(sm.A[i][j], r), df_mul(sm.A[l][j], r));
+                sm.A[i][l] = v;
+                if (e == 0) {  // the next pivot is final: take its reciprocal square root now
+                    if (!(v.hi > static_cast<float>(PIVOT_REL) * sm.swd[j + 1]) || !(v.hi > 0.0f)) {
+                        sm.fail = CVA_ERR_NOT_SPD;
+                    } else {
+                        const df rr = df_rsqrt(v);
+                        sm.invd[j + 1] = rr;
+                        sm.L[j + 1][j + 1] = df_mul(v, rr);
+                    }
+                }
+            } else if (e < ntri + m * K) {
+                const int q = e - ntri;
+                const int i = j + 1 + q / K, c = q - (q / K) * K;
+                sm.A[i][B + c] = df_fms(sm.A[i][B + c], df_mul(sm.A[i][j], r), df_mul(sm.A[j][B + c], r));
+            } else if (e < ntri + m * K + m) {
+                const int i = j + 1 + (e - ntri - m * K);
+                sm.L[i][j] = df_mul(sm.A[i][j], r);
             } else {
-                const int q = e - na - nbk - nc;
-                const int i = j + 1 + q / K, c = q % K;
-                sm.A[i][B + c] -= sm.A[i][j] * sm.A[j][B + c] * r2;
+                const int c = e - ntri - m * K - m;
+                sm.G[j][c] = df_mul(sm.A[j][B + c], r);
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
     if (sm.fail) {
         if (tid == 0) set_status(dm, sm.fail);
         return;
     }
     for (int e = tid; e < B * B; e += TPB) {
         const int i = e / B, j = e - (e / B) * B;
-        dm->L[i][j] = sm.L[i][j];
+        dm->L[i][j] = df_to_double(sm.L[i][j]);
     }
-    if (tid < B) dm->Linvd[tid] = sm.invd[tid];
+    if (tid < B) dm->Linvd[tid] = df_to_double(sm.invd[tid]);
 
-    // ---- 3. T = G^T G scaled to unit Frobenius norm, then Jacobi -------------
-    for (int e = tid; e < K * K; e += TPB) {
-        const int a = e / K, b = e - (e / K) * K;
-        double s = 0.0;
-        for (int i = 0; i < B; ++i) s += sm.G[i][a] * sm.G[i][b];
-        sm.T[a][b] = s;
+    // ---- 3. T = G^T G, scaled by a power of two to about unit norm ----------
+    {
+        const int KK = K * K;
+        int per = 1;
+        while (per * 2 * KK <= TPB && per < 32) per *= 2;
+        const int e = tid / per, sub = tid - (tid / per) * per;
+        df s = df_from(0.0f);
+        if (e < KK) {
+            const int a = e / K, b = e - (e / K) * K;
+            for (int i = sub; i < B; i += per) s = df_fma(s, sm.G[i][a], sm.G[i][b]);
+        }
+        for (int o = per / 2; o > 0; o >>= 1) s = df_add(s, shfl_xor_df(s, o));
+        if (e < KK && sub == 0) sm.T[e / K][e % K] = s;
     }
     __syncthreads();
     if (tid < 32) {
-        double s = 0.0;
-        for (int e = tid; e < K * K; e += 32) s += sm.T[e / K][e % K] * sm.T[e / K][e % K];
-        s = warp_sum(s);
-        if (tid == 0) sm.fro = sqrt(s);
+        float f = 0.0f;
+        for (int e = tid; e < K * K; e += 32) f = fmaf(sm.T[e / K][e % K].hi, sm.T[e / K][e % K].hi, f);
+        f = warp_sumf(f);
+        if (tid == 0) {
+            int ex = 0;
+            if (f > 0.0f) frexpf(sqrtf(f), &ex);
+            sm.scale = pow2f(-ex);
+        }
     }
     __syncthreads();
-    const double fro = sm.fro;
-    if (fro > 0.0) {
-        const double inv = 1.0 / fro;
-        for (int e = tid; e < K * K; e += TPB) sm.T[e / K][e % K] *= inv;
+    const float scale = sm.scale;
+    if (tid < K * K) {
+        const int a = tid / K, b = tid % K;
+        sm.T[a][b] = df_mulf(sm.T[a][b], scale);  // exact: a power of two
+        sm.Tf[a][b] = sm.T[a][b].hi;
+        sm.Wf[a][b] = (a == b) ? 1.0f : 0.0f;
     }
     __syncthreads();
-    if (tid < 32) {
-        const int lane = tid;
-        for (int e = lane; e < K * K; e += 32) sm.Wv[e / K][e % K] = (e / K == e % K) ? 1.0 : 0.0;
-        __syncwarp();
+
+    // ---- 4. FP32 cyclic Jacobi on T, then 5. refinement (one warp) ----------
+    if (warp == 0) {
         const int n = K + (K & 1), half = n / 2;
-        bool converged = false;
-        for (int sweep = 0; sweep <= MAX_SWEEPS; ++sweep) {
-            double off = 0.0;
+        for (int e = lane; e < (n - 1) * n; e += 32) {  // round-robin seating, one row per round
+            const int round = e / n, seat = e - (e / n) * n;
+            sm.rr[round][seat] = static_cast<unsigned char>(rr_player(seat, round, n));
+        }
+        float tot = 0.0f;
+        for (int e = lane; e < K * K; e += 32) tot = fmaf(sm.Tf[e / K][e % K], sm.Tf[e / K][e % K], tot);
+        tot = warp_sumf(tot);
+        __syncwarp();
+        float prev = 3.0e38f;
+        for (int sweep = 0; sweep < JACOBI_SWEEPS; ++sweep) {
+            float off = 0.0f;
             for (int e = lane; e < K * K; e += 32) {
                 const int a = e / K, b = e % K;
-                if (a != b) off += sm.T[a][b] * sm.T[a][b];
+                if (a != b) off = fmaf(sm.Tf[a][b], sm.Tf[a][b], off);
             }
-            off = warp_sum(off);
-            if (off <= OFF_TOL2) { converged = true; break; }
-            if (sweep == MAX_SWEEPS) break;
+            off = warp_sumf(off);
+            if (off <= 1e-11f * tot || off >= 0.25f * prev) break;  // converged, or stalled at FP32 rounding
+            prev = off;
             for (int round = 0; round < n - 1; ++round) {
                 if (lane < half) {
-                    const int a = rr_player(lane, round, n), b = rr_player(n - 1 - lane, round, n);
+                    const int a = sm.rr[round][lane], b = sm.rr[round][n - 1 - lane];
                     const int p = min(a, b), q = max(a, b);
                     int ok = 0;
-                    double cs = 1.0, sn = 0.0;
+                    float cs = 1.0f, sn = 0.0f;
                     if (q < K) {
-                        const float apq = static_cast<float>(sm.T[p][q]);
+                        const float apq = sm.Tf[p][q];
                         if (apq != 0.0f) {
-                            const float tau = static_cast<float>(sm.T[q][q] - sm.T[p][p]) / (2.0f * apq);
+                            const float tau = (sm.Tf[q][q] - sm.Tf[p][p]) / (2.0f * apq);
                             float t;
                             if (fabsf(tau) > 1e15f) t = 0.5f / tau;
                             else t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
-                            const double td = static_cast<double>(t);
-                            cs = rsqrt_fp64(fma(td, td, 1.0));
-                            sn = td * cs;
+                            cs = rsqrtf(fmaf(t, t, 1.0f));
+                            sn = t * cs;
                             ok = 1;
                         }
                     }
-                    sm.rot_p[lane] = p;
-                    sm.rot_q[lane] = q;
-                    sm.rot_c[lane] = cs;
-                    sm.rot_s[lane] = sn;
-                    sm.rot_ok[lane] = ok;
+                    sm.rp[lane] = p;
+                    sm.rq[lane] = q;
+                    sm.rc[lane] = cs;
+                    sm.rs[lane] = sn;
+                    sm.rok[lane] = ok;
                 }
                 __syncwarp();
-                for (int e = lane; e < K * half; e += 32) {  // T <- T J (columns p, q)
+                for (int e = lane; e < K * half; e += 32) {  // T <- T J
                     const int r = e % K, w = e / K;
-                    if (!sm.rot_ok[w]) continue;
-                    const int p = sm.rot_p[w], q = sm.rot_q[w];
-                    const double cs = sm.rot_c[w], sn = sm.rot_s[w];
-                    const double a = sm.T[r][p], b = sm.T[r][q];
-                    sm.T[r][p] = cs * a - sn * b;
-                    sm.T[r][q] = sn * a + cs * b;
+                    if (!sm.rok[w]) continue;
+                    const int p = sm.rp[w], q = sm.rq[w];
+                    const float cs = sm.rc[w], sn = sm.rs[w];
+                    const float a = sm.Tf[r][p], b = sm.Tf[r][q];
+                    sm.Tf[r][p] = cs * a - sn * b;
+                    sm.Tf[r][q] = sn * a + cs * b;
                 }
                 __syncwarp();
-                for (int e = lane; e < K * half; e += 32) {  // T <- J^T T (rows), W <- W J
+                for (int e = lane; e < K * half; e += 32) {  // T <- J^T T, W <- W J
                     const int r = e % K, w = e / K;
-                    if (!sm.rot_ok[w]) continue;
-                    const int p = sm.rot_p[w], q = sm.rot_q[w];
-                    const double cs = sm.rot_c[w], sn = sm.rot_s[w];
-                    const double a = sm.T[p][r], b = sm.T[q][r];
-                    sm.T[p][r] = cs * a - sn * b;
-                    sm.T[q][r] = sn * a + cs * b;
-                    const double wa = sm.Wv[r][p], wb = sm.Wv[r][q];
-                    sm.Wv[r][p] = cs * wa - sn * wb;
-                    sm.Wv[r][q] = sn * wa + cs * wb;
+                    if (!sm.rok[w]) continue;
+                    const int p = sm.rp[w], q = sm.rq[w];
+                    const float cs = sm.rc[w], sn = sm.rs[w];
+                    const float a = sm.Tf[p][r], b = sm.Tf[q][r];
+                    sm.Tf[p][r] = cs * a - sn * b;
+                    sm.Tf[q][r] = sn * a + cs * b;
+                    const float wa = sm.Wf[r][p], wb = sm.Wf[r][q];
+                    sm.Wf[r][p] = cs * wa - sn * wb;
+                    sm.Wf[r][q] = sn * wa + cs * wb;
                 }
                 __syncwarp();
             }
         }
-        if (lane == 0) {
-            if (!converged) sm.fail = CVA_ERR_NO_CONVERGENCE;
-            // eigenvalues in descending order (selection, lowest index first on ties)
-            int used = 0;
-            for (int j = 0; j < K; ++j) {
-                int best = -1;
-                for (int i = 0; i < K; ++i) {
-                    if (used & (1 << i)) continue;
-                    if (best < 0 || sm.T[i][i] > sm.T[best][best]) best = i;
+
+        // Ogita-Aishima refinement of the eigenvectors W of T in double-float
+        for (int e = lane; e < K * K; e += 32) sm.W[e / K][e % K] = df_from(sm.Wf[e / K][e % K]);
+        __syncwarp();
+        for (int it = 0; it < REFINE_STEPS; ++it) {
+            for (int e = lane; e < K * K; e += 32) {
+                const int a = e / K, b = e % K;
+                df r = df_from(0.0f), tw = df_from(0.0f);
+                for (int k = 0; k < K; ++k) {
+                    r = df_fma(r, sm.W[k][a], sm.W[k][b]);     // W^T W
+                    tw = df_fma(tw, sm.T[a][k], sm.W[k][b]);   // T W
                 }
-                used |= 1 << best;
-                sm.order[j] = best;
+                sm.R[a][b] = df_sub(df_from(a == b ? 1.0f : 0.0f), r);  // I - W^T W
+                sm.TW[a][b] = tw;
             }
-            const int rmax = min(K - 1, B);
-            const double top = sm.T[sm.order[0]][sm.order[0]];
-            int r = 0;
-            while (r < rmax && top > 0.0 && sm.T[sm.order[r]][sm.order[r]] > 1e-12 * top) ++r;
-            sm.r_eff = r;
-            for (int j = 0; j < B; ++j) sm.lam[j] = (j < r) ? sm.T[sm.order[j]][sm.order[j]] * fro : 0.0;
+            __syncwarp();
+            float so = 0.0f, lm = 0.0f, rm = 0.0f;
+            for (int e = lane; e < K * K; e += 32) {
+                const int a = e / K, b = e % K;
+                df sv = df_from(0.0f);
+                for (int k = 0; k < K; ++k) sv = df_fma(sv, sm.W[k][a], sm.TW[k][b]);  // W^T T W
+                sm.S[a][b] = sv;
+                if (a != b) so = fmaxf(so, fabsf(sv.hi));
+                else lm = fmaxf(lm, fabsf(sv.hi));
+                rm = fmaxf(rm, fabsf(sm.R[a][b].hi));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                so = fmaxf(so, __shfl_xor_sync(0xFFFFFFFFu, so, o));
+                lm = fmaxf(lm, __shfl_xor_sync(0xFFFFFFFFu, lm, o));
+                rm = fmaxf(rm, __shfl_xor_sync(0xFFFFFFFFu, rm, o));
+            }
+            const float delta = 2.0f * (so + lm * rm);  // cluster threshold
+            __syncwarp();
+            if (lane < K) {  // lambda_i = s_ii / (1 - r_ii) = s_ii (1 + r_ii + r_ii^2 + ...)
+                const df r = sm.R[lane][lane];
+                sm.lamk[lane] = df_mul(sm.S[lane][lane], df_add(df_from(1.0f), df_mul(r, df_add(df_from(1.0f), r))));
+            }
+            __syncwarp();
+            for (int e = lane; e < K * K; e += 32) {
+                const int a = e / K, b = e % K;
+                df ev;
+                const df gap = df_sub(sm.lamk[b], sm.lamk[a]);
+                if (a == b || fabsf(gap.hi) <= delta) {
+                    ev = df_mulf(sm.R[a][b], 0.5f);
+                } else {
+                    const df num = df_fma(sm.S[a][b], sm.lamk[b], sm.R[a][b]);
+                    ev = df_from(num.hi / gap.hi);
+                }
+                sm.E[a][b] = ev;
+            }
+            __syncwarp();
+            for (int e = lane; e < K * K; e += 32) {
+                const int a = e / K, b = e % K;
+                df d = df_from(0.0f);
+                for (int k = 0; k < K; ++k) d = df_fma(d, sm.W[a][k], sm.E[k][b]);  // W E
+                sm.TW[a][b] = d;
+            }
+            __syncwarp();
+            for (int e = lane; e < K * K; e += 32) sm.W[e / K][e % K] = df_add(sm.W[e / K][e % K], sm.TW[e / K][e % K]);
+            __syncwarp();
         }
     }
     __syncthreads();
-    if (sm.fail) {
-        if (tid == 0) set_status(dm, sm.fail);
-        return;
-    }
-    const int r = sm.r_eff;
-    const int nv = nvec > B ? B : nvec;
 
-    // ---- 4. whitened eigenvectors, completed where lambda = 0 --------------
+    // ---- 6. eigenvalues in descending order, whitened eigenvectors ----------
+    if (tid == 0) {
+        int used = 0;
+        for (int j = 0; j < K; ++j) {
+            int best = -1;
+            for (int i = 0; i < K; ++i) {
+                if (used & (1 << i)) continue;
+                if (best < 0 || df_gt(sm.lamk[i], sm.lamk[best])) best = i;
+            }
+            used |= 1 << best;
+            sm.order[j] = best;
+        }
+        const int rmax = min(K - 1, B);
+        const float top = sm.lamk[sm.order[0]].hi;
+        int r = 0;
+        while (r < rmax && top > 0.0f && sm.lamk[sm.order[r]].hi > 1e-12f * top) ++r;
+        sm.r_eff = r;
+    }
+    __syncthreads();
+    const int r = sm.r_eff;
+    const float unscale = __frcp_rn(scale);  // a power of two: exact
+    if (tid < B) sm.lam[tid] = (tid < r) ? df_mulf(sm.lamk[sm.order[tid]], unscale) : df_from(0.0f);
+    const int nv = nvec > B ? B : nvec;
     const int rr = r < nv ? r : nv;
+    __syncthreads();
     for (int e = tid; e < B * rr; e += TPB) {
         const int b = e / rr, j = e - (e / rr) * rr;
         const int w = sm.order[j];
-        double s = 0.0;
-        for (int c = 0; c < K; ++c) s += sm.G[b][c] * sm.Wv[c][w];
-        sm.U[b][j] = s * rsqrt_fp64(sm.lam[j]);
+        df s = df_from(0.0f);
+        for (int c = 0; c < K; ++c) s = df_fma(s, sm.G[b][c], sm.W[c][w]);
+        sm.U[b][j] = df_mul(s, df_rsqrt(sm.lam[j]));
     }
     __syncthreads();
     if (nv > r) complete_basis(sm, B, r, nv);
     const int ncols = nv;
 
-    // ---- 5. V = L^-T U by right-looking back substitution -------------------
+    // ---- 7. V = L^-T U: back substitution, one barrier per row -----------------
     for (int e = tid; e < B * ncols; e += TPB) {
         const int b = e / ncols, j = e - (e / ncols) * ncols;
         sm.A[b][j] = sm.U[b][j];
+        if (b == B - 1) sm.V[b][j] = df_mul(sm.U[b][j], sm.invd[b]);
     }
-    __syncthreads();
-    for (int i = B - 1; i >= 0; --i) {
-        if (tid < ncols) sm.V[i][tid] = sm.A[i][tid] * sm.invd[i];
+    for (int i = B - 1; i > 0; --i) {
         __syncthreads();
         for (int e = tid; e < i * ncols; e += TPB) {
             const int l = e / ncols, j = e - (e / ncols) * ncols;
-            sm.A[l][j] -= sm.L[i][l] * sm.V[i][j];
+            const df v = df_fms(sm.A[l][j], sm.L[i][l], sm.V[i][j]);
+            sm.A[l][j] = v;
+            if (l == i - 1) sm.V[l][j] = df_mul(v, sm.invd[l]);
         }
-        __syncthreads();
-    }
-
-    // sign convention: largest-magnitude component positive, lowest band on ties
-    if (tid < ncols) {
-        const int j = tid;
-        double big = 0.0;
-        for (int b = 0; b < B; ++b) big = fmax(big, fabs(sm.V[b][j]));
-        int arg = 0;
-        for (int b = 0; b < B; ++b)
-            if (fabs(sm.V[b][j]) >= big * (1.0 - TIE_REL)) { arg = b; break; }
-        if (sm.V[arg][j] < 0.0)
-            for (int b = 0; b < B; ++b) { sm.V[b][j] = -sm.V[b][j]; sm.U[b][j] = -sm.U[b][j]; }
     }
     __syncthreads();
 
-    // ---- 6. publish: FP64 results, FP32 coefficients, range sentinels ------
+    // ---- 8. sign convention ---------------------------------------------------
+    for (int j = warp; j < ncols; j += NWARP) {
+        const df v = lane < B ? sm.V[lane][j] : df_from(0.0f);
+        const df av = df_abs(v);
+        df big = av;
+        for (int o = 16; o > 0; o >>= 1) {
+            const df other = shfl_xor_df(big, o);
+            if (df_gt(other, big)) big = other;
+        }
+        const df thr = df_mul(big, df_make(1.0f, -static_cast<float>(TIE_REL)));
+        const unsigned ties = __ballot_sync(0xFFFFFFFFu, lane < B && df_ge(av, thr));
+        const int arg = __ffs(ties) - 1;
+        const float sh_hi = __shfl_sync(0xFFFFFFFFu, v.hi, arg);
+        const float sh_lo = __shfl_sync(0xFFFFFFFFu, v.lo, arg);
+        const bool neg = sh_hi < 0.0f || (sh_hi == 0.0f && sh_lo < 0.0f);
+        if (neg && lane < B) {
+            sm.V[lane][j] = df_neg(sm.V[lane][j]);
+            sm.U[lane][j] = df_neg(sm.U[lane][j]);
+        }
+    }
+    __syncthreads();
+
+    // ---- 9. publish: FP64 results, FP32 coefficients, range sentinels --------
     for (int e = tid; e < MAXB * MAXB; e += TPB) {
         const int b = e / MAXB, j = e - (e / MAXB) * MAXB;
         const bool live = b < B && j < ncols;
-        dm->V[b][j] = live ? sm.V[b][j] : 0.0;
-        dm->U[b][j] = live ? sm.U[b][j] : 0.0;
-        dm->Vf[b][j] = live ? static_cast<float>(sm.V[b][j]) : 0.0f;
+        dm->V[b][j] = live ? df_to_double(sm.V[b][j]) : 0.0;
+        dm->U[b][j] = live ? df_to_double(sm.U[b][j]) : 0.0;
+        dm->Vf[b][j] = live ? sm.V[b][j].hi : 0.0f;
     }
     if (tid < MAXB) {
-        dm->lam[tid] = tid < B ? sm.lam[tid] : 0.0;
-        const double m = tid < B ? rint(dm->mu[tid]) : 0.0;
-        dm->shift[tid] = MAGIC_2P23 + static_cast<float>(m);
+        dm->lam[tid] = tid < B ? df_to_double(sm.lam[tid]) : 0.0;
+        const float m = tid < B ? rintf(sm.mu[tid].hi) : 0.0f;
+        dm->shift[tid] = MAGIC_2P23 + m;
         dm->train_range[2 * tid] = __int_as_float(0x7F800000);       // +inf
         dm->train_range[2 * tid + 1] = __int_as_float(0xFF800000);   // -inf
     }
-    if (tid < ncols) {
-        double s = 0.0;
-        for (int b = 0; b < B; ++b) s += sm.V[b][tid] * (dm->mu[b] - rint(dm->mu[b]));
-        dm->dofs[tid] = static_cast<float>(s);
-    } else if (tid < MAXB) {
-        dm->dofs[tid] = 0.0f;
+    for (int j = warp; j < MAXB; j += NWARP) {
+        df s = df_from(0.0f);
+        if (j < ncols && lane < B) s = df_mul(sm.V[lane][j], df_sub(sm.mu[lane], df_from(rintf(sm.mu[lane].hi))));
+        if (j < ncols) s = warp_sum_df(s);
+        if (lane == 0) dm->dofs[j] = j < ncols ? s.hi : 0.0f;
     }
     if (tid == 0) {
         dm->r = r;
         dm->nvec = ncols;
         dm->fitted = 1;
+    }
+}
+
+// Sb = Mb Mb^T for the statistics getter (not on the fit path).
+__global__ void k_scatter_sb(DevModel* __restrict__ dm, int B, int K)
+{
+    for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+        const int i = e / B, j = e % B;
+        double s = 0.0;
+        for (int c = 0; c < K; ++c) s = fma(dm->Mb[i][c], dm->Mb[j][c], s);
+        dm->Sb[i][j] = s;
     }
 }
 
@@ -470,6 +599,12 @@ cudaError_t launch_fit_finalize(DevModel* dm, int B, int K, int nvec, cudaStream
     cudaError_t e = cudaFuncSetAttribute(k_fit_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_fit_finalize<<<1, TPB, smem, s>>>(dm, B, K, nvec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_sb(DevModel* dm, int B, int K, cudaStream_t s)
+{
+    k_scatter_sb<<<1, 256, 0, s>>>(dm, B, K);
     return cudaGetLastError();
 }
 

@@ -219,52 +219,54 @@ k_project_s(const uint16_t* __restrict__ cube, int B, long long P, long long p_b
 }
 
 // Training-score range of variates [j0, j0 + kc): same FP32 operations as the
-// projection, on the labelled pixels only.
+// projection, on the rows of the gathered training matrix (x_0 .. x_{B-1}, 1, 0 ..).
+template <int KV>
 __global__ void __launch_bounds__(TPB)
-k_train_range(const uint16_t* __restrict__ cube, int B, long long P, const uint8_t* __restrict__ labels,
-              int K, int vec_labels, DevModel* __restrict__ dm, int j0, int kc)
+k_train_range(int B, int K, const uint16_t* __restrict__ xtr, DevModel* __restrict__ dm, int j0)
 {
-    __shared__ ProjSmem<KCH> sm;
+    __shared__ ProjSmem<KV> sm;
     if (dm->status != 0 || !dm->fitted) return;
-    load_coefs<KCH>(sm, dm, B, j0, kc, nullptr, false);
+    load_coefs<KV>(sm, dm, B, j0, KV, nullptr, false);
     __syncthreads();
-    float mn[KCH], mx[KCH];
+    unsigned int N = 0;
+    for (int c = 0; c < K; ++c) N += dm->cls_count[c];
+    const int BR = xtr_row(B);
+    float mn[KV], mx[KV];
     #pragma unroll
-    for (int j = 0; j < KCH; ++j) { mn[j] = __int_as_float(0x7F800000); mx[j] = __int_as_float(0xFF800000); }
-    constexpr int TILE = TPB * 16;
-    for (long long tile = blockIdx.x; tile * TILE < P; tile += gridDim.x) {
-        const long long p0 = tile * TILE + 16LL * threadIdx.x;
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
-        if (vec_labels && p0 + 16 <= P) {
-            const uint4 v = __ldcs(reinterpret_cast<const uint4*>(labels + p0));
-            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
-        } else {
-            for (int i = 0; i < 16; ++i)
-                if (p0 + i < P) w[i >> 2] |= static_cast<uint32_t>(labels[p0 + i]) << (8 * (i & 3));
+    for (int j = 0; j < KV; ++j) { mn[j] = __int_as_float(0x7F800000); mx[j] = __int_as_float(0xFF800000); }
+    const unsigned int stride = gridDim.x * TPB;
+    for (unsigned int i = blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
+        const uint4* row = reinterpret_cast<const uint4*>(xtr + static_cast<long long>(i) * BR);
+        uint32_t pk[(MAXB + 8) / 2];
+        #pragma unroll
+        for (int q = 0; q < (MAXB + 8) / 8; ++q) {
+            if (q * 8 < BR) {
+                const uint4 v = __ldg(row + q);
+                pk[4 * q] = v.x; pk[4 * q + 1] = v.y; pk[4 * q + 2] = v.z; pk[4 * q + 3] = v.w;
+            } else {
+                pk[4 * q] = pk[4 * q + 1] = pk[4 * q + 2] = pk[4 * q + 3] = 0u;
+            }
         }
-        if ((w[0] | w[1] | w[2] | w[3]) == 0u) continue;
-        for (int i = 0; i < 16; ++i) {
-            const uint32_t l = (w[i >> 2] >> (8 * (i & 3))) & 0xFFu;
-            if (l == 0u || l > static_cast<uint32_t>(K)) continue;
-            const long long p = p0 + i;
-            float acc[KCH];
-            #pragma unroll
-            for (int j = 0; j < KCH; ++j) acc[j] = 0.0f;
-            for (int b = 0; b < B; ++b) {
-                const uint32_t x = __ldg(cube + static_cast<long long>(b) * P + p);
-                const float xs = __fsub_rn(u16_biased(x), sm.shift[b]);
+        float acc[KV];
+        #pragma unroll
+        for (int j = 0; j < KV; ++j) acc[j] = 0.0f;
+        #pragma unroll
+        for (int b = 0; b < MAXB; ++b) {
+            if (b < B) {
+                const uint32_t w = pk[b >> 1];
+                const float xs = __fsub_rn((b & 1) ? u16_hi_biased(w) : u16_lo_biased(w), sm.shift[b]);
                 #pragma unroll
-                for (int j = 0; j < KCH; ++j) acc[j] = __fmaf_rn(sm.V[b][j], xs, acc[j]);
+                for (int j = 0; j < KV; ++j) acc[j] = __fmaf_rn(sm.V[b][j], xs, acc[j]);
             }
-            #pragma unroll
-            for (int j = 0; j < KCH; ++j) {
-                const float y = __fsub_rn(acc[j], sm.d[j]);
-                mn[j] = fminf(mn[j], y);
-                mx[j] = fmaxf(mx[j], y);
-            }
+        }
+        #pragma unroll
+        for (int j = 0; j < KV; ++j) {
+            const float y = __fsub_rn(acc[j], sm.d[j]);
+            mn[j] = fminf(mn[j], y);
+            mx[j] = fmaxf(mx[j], y);
         }
     }
-    reduce_range<KCH>(sm, mn, mx, kc, dm->train_range, j0);
+    reduce_range<KV>(sm, mn, mx, KV, dm->train_range, j0);
 }
 
 __global__ void k_range_init(float* range, int k)
@@ -404,17 +406,22 @@ cudaError_t launch_range_init(float* range, int k, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_train_range(const uint16_t* cube, int B, long long P, const uint8_t* labels, int K,
-                               DevModel* dm, int nvec, int num_sms, cudaStream_t s)
+cudaError_t launch_train_range(int B, int K, const uint16_t* xtr, DevModel* dm, int nvec, int num_sms,
+                               cudaStream_t s)
 {
-    const long long tiles = (P + TPB * 16 - 1) / (TPB * 16);
-    long long grid = static_cast<long long>(num_sms) * 4;
-    if (grid > tiles) grid = tiles;
-    if (grid < 1) grid = 1;
-    const int vec = (reinterpret_cast<uintptr_t>(labels) % 16 == 0) ? 1 : 0;
+    const unsigned grid = static_cast<unsigned>(num_sms) * 4;
     for (int j0 = 0; j0 < nvec; j0 += KCH) {
         const int kc = (nvec - j0) < KCH ? (nvec - j0) : KCH;
-        k_train_range<<<static_cast<unsigned>(grid), TPB, 0, s>>>(cube, B, P, labels, K, vec, dm, j0, kc);
+        switch (kc) {
+            case 1: k_train_range<1><<<grid, TPB, 0, s>>>(B, K, xtr, dm, j0); break;
+            case 2: k_train_range<2><<<grid, TPB, 0, s>>>(B, K, xtr, dm, j0); break;
+            case 3: k_train_range<3><<<grid, TPB, 0, s>>>(B, K, xtr, dm, j0); break;
+            case 4: k_train_range<4><<<grid, TPB, 0, s>>>(B, K, xtr, dm, j0); break;
+            case 5: k_train_range<5><<<grid, TPB, 0, s>>>(B, K, xtr, dm, j0); break;
+            case 6: k_train_range<6><<<grid, TPB, 0, s>>>(B, K, xtr, dm, j0); break;
+            case 7: k_train_range<7><<<grid, TPB, 0, s>>>(B, K, xtr, dm, j0); break;
+            default: k_train_range<8><<<grid, TPB, 0, s>>>(B, K, xtr, dm, j0); break;
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

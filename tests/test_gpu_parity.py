@@ -306,3 +306,24 @@ def test_full_size_23_band_4096x4096_cube():
     cva.cva_project(cube, m, w.k, out_f32=y)
     assert _normwise(y.cpu().numpy().reshape(w.k, -1), y_ref) <= 1e-4
     m.close()
+
+
+def test_training_capacity_is_checked_on_device():
+    """More training pixels than the model's buffer holds is a device error
+    (no out-of-bounds writes); reserving room fixes it."""
+    _skip_without_gpu()
+    H, W = 2100, 2100  # 4.41 M labelled pixels > the default 4 M capacity
+    rng = np.random.default_rng(5)
+    cube = torch.from_numpy(rng.integers(0, 4096, size=(2, H, W)).astype(np.uint16)).to(DEV)
+    lab = np.ones((H, W), np.uint8)
+    lab[:, ::2] = 2
+    labels = torch.from_numpy(lab).to(DEV)
+    m = cva.Model(2, 2)
+    cva.cva_fit(cube, labels, 2, m)
+    assert cva.cva_status(m) == cva.CVA_ERR_CAPACITY
+    cva.cva_model_reserve(m, H * W)
+    cva.cva_fit(cube, labels, 2, m)
+    assert cva.cva_status(m) == cva.CVA_OK
+    n, mc, Sw, Sb = cva.cva_model_get_scatter(m)
+    assert n.tolist() == [H * W - H * ((W + 1) // 2), H * ((W + 1) // 2)]
+    m.close()
