@@ -18,8 +18,9 @@ struct cva_model {
     int precision;
     cva::DevModel* dm;
     unsigned int* tiles; // per-tile class counts, then first rows (MAX_TILES x (K + 1))
+    unsigned int* list;  // class-major training-pixel indices, cap entries
     uint16_t* xtr;       // gathered training matrix, cap rows of xtr_row(B)
-    long long cap;       // rows of `xtr`
+    long long cap;       // training pixels `list` and `xtr` hold
 };
 
 namespace {
@@ -94,14 +95,17 @@ int cva_model_create(int B, int K, cva_model** out)
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CVA_ERR_CUDA;
     DevModel* dm = nullptr;
     unsigned int* tiles = nullptr;
+    unsigned int* list = nullptr;
     uint16_t* xtr = nullptr;
     const size_t cap = CVA_DEFAULT_TRAIN_CAPACITY;
     if (cudaMalloc(&dm, sizeof(DevModel)) != cudaSuccess) return CVA_ERR_CUDA;
     if (cudaMalloc(&tiles, sizeof(unsigned int) * static_cast<size_t>(cva::MAX_TILES) * (K + 1)) != cudaSuccess ||
+        cudaMalloc(&list, sizeof(unsigned int) * cap) != cudaSuccess ||
         cudaMalloc(&xtr, sizeof(uint16_t) * cap * cva::xtr_row(B)) != cudaSuccess ||
         cudaMemset(dm, 0, sizeof(DevModel)) != cudaSuccess) {
         cudaFree(dm);
         cudaFree(tiles);
+        cudaFree(list);
         cudaFree(xtr);
         return CVA_ERR_CUDA;
     }
@@ -109,6 +113,7 @@ int cva_model_create(int B, int K, cva_model** out)
     if (!m) {
         cudaFree(dm);
         cudaFree(tiles);
+        cudaFree(list);
         cudaFree(xtr);
         return CVA_ERR_INVALID_ARG;
     }
@@ -120,6 +125,7 @@ int cva_model_create(int B, int K, cva_model** out)
     m->precision = CVA_PRECISION_EXACT;
     m->dm = dm;
     m->tiles = tiles;
+    m->list = list;
     m->xtr = xtr;
     m->cap = static_cast<long long>(cap);
     *out = m;
@@ -131,10 +137,16 @@ int cva_model_reserve(cva_model* m, int64_t max_train)
     if (!m || max_train < 1 || max_train >= (1LL << 31)) return CVA_ERR_INVALID_ARG;
     if (max_train <= m->cap) return CVA_OK;
     if (cudaDeviceSynchronize() != cudaSuccess) return CVA_ERR_CUDA;
+    unsigned int* list = nullptr;
     uint16_t* xtr = nullptr;
-    if (cudaMalloc(&xtr, sizeof(uint16_t) * static_cast<size_t>(max_train) * cva::xtr_row(m->B)) != cudaSuccess)
+    if (cudaMalloc(&list, sizeof(unsigned int) * static_cast<size_t>(max_train)) != cudaSuccess) return CVA_ERR_CUDA;
+    if (cudaMalloc(&xtr, sizeof(uint16_t) * static_cast<size_t>(max_train) * cva::xtr_row(m->B)) != cudaSuccess) {
+        cudaFree(list);
         return CVA_ERR_CUDA;
+    }
+    cudaFree(m->list);
     cudaFree(m->xtr);
+    m->list = list;
     m->xtr = xtr;
     m->cap = max_train;
     return CVA_OK;
@@ -146,6 +158,7 @@ void cva_model_destroy(cva_model* m)
     cudaDeviceSynchronize();
     cudaFree(m->dm);
     cudaFree(m->tiles);
+    cudaFree(m->list);
     cudaFree(m->xtr);
     delete m;
 }
@@ -172,7 +185,8 @@ int cva_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, in
     if (!device_visible(cube) || !device_visible(labels)) return CVA_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long P = static_cast<long long>(H) * W;
-    cudaError_t e = cva::launch_fit_moments(cube, B, P, labels, K, m->dm, m->xtr, m->tiles, m->cap, m->num_sms, s);
+    cudaError_t e =
+        cva::launch_fit_moments(cube, B, P, labels, K, m->dm, m->xtr, m->tiles, m->list, m->cap, m->num_sms, s);
     if (e == cudaSuccess) e = cva::launch_fit_finalize(m->dm, B, K, m->nvec, s);
     if (e == cudaSuccess) e = cva::launch_train_range(B, K, m->xtr, m->dm, m->nvec, m->num_sms, s);
     return from_cuda(e);

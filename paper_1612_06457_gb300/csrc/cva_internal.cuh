@@ -64,6 +64,7 @@ struct DevModel {
     int r;        // eigenpairs taken from the reduced K x K problem
     int nvec;     // canonical vectors formed (columns of V)
     unsigned int cls_count[MAXK];   // training pixels per class
+    unsigned int tile_ticket;       // CTAs of the label count done (the last one scans)
 
     // ---- fit results --------------------------------------------------------
     long long n[MAXK];          // training pixels per class
@@ -101,12 +102,13 @@ __host__ __device__ inline int xtr_row(int B)
 }
 
 // Training-pixel passes: per-tile class counts (`tiles`: ceil(P / LABEL_TILE)
-// rows of K + 1 words), their prefix sums, the gather of every training
-// pixel's bands into the class-major matrix `xtr` (`cap` rows of
-// xtr_row(B)), then the exact moments from it.
+// rows of K + 1 words) and their prefix sums, the class-major pixel list
+// (`list`, `cap` entries), the gather of every training pixel's bands into
+// the class-major matrix `xtr` (`cap` rows of xtr_row(B)), then the exact
+// moments from it.
 cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const uint8_t* labels,
-                               int K, DevModel* dm, uint16_t* xtr, unsigned int* tiles, long long cap,
-                               int num_sms, cudaStream_t s);
+                               int K, DevModel* dm, uint16_t* xtr, unsigned int* tiles, unsigned int* list,
+                               long long cap, int num_sms, cudaStream_t s);
 cudaError_t launch_fit_finalize(DevModel* dm, int B, int K, int nvec, cudaStream_t s);
 cudaError_t launch_train_range(int B, int K, const uint16_t* xtr, DevModel* dm, int nvec, int num_sms,
                                cudaStream_t s);

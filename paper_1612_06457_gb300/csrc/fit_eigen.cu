@@ -48,13 +48,14 @@ namespace {
 constexpr int TPB = 256;
 constexpr int NWARP = TPB / 32;
 constexpr int JACOBI_SWEEPS = 40;
-constexpr int REFINE_STEPS = 2;
+constexpr int REFINE_STEPS = 3;
 constexpr int MAXTRI = MAXB * (MAXB + 1) / 2;
 
 struct FinSmem {
-    df A[MAXB][MAXB + MAXK + 1];  // [Sw | Mb] during elimination, then back-substitution work
+    df A[MAXB][2 * MAXB + MAXK + 1];  // [Sw | Mb | I] during elimination
     df L[MAXB][MAXB + 1];
     df G[MAXB][MAXK + 1];
+    df Li[MAXB][MAXB + 1];        // L^-1 (lower triangular)
     df T[MAXK][MAXK + 1];
     df W[MAXK][MAXK + 1];
     df R[MAXK][MAXK + 1];
@@ -247,10 +248,17 @@ __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm,
     }
     __syncthreads();
     if (tid < B) sm.swd[tid] = sm.A[tid][tid].hi;
-    for (int e = tid; e < MAXB * (MAXB + 1); e += TPB) (&sm.L[0][0])[e] = df_from(0.0f);
+    for (int e = tid; e < MAXB * (MAXB + 1); e += TPB) {
+        (&sm.L[0][0])[e] = df_from(0.0f);
+        (&sm.Li[0][0])[e] = df_from(0.0f);
+    }
+    for (int e = tid; e < B * B; e += TPB) {  // identity columns: the elimination turns them into L^-1
+        const int i = e / B, j = e - (e / B) * B;
+        sm.A[i][B + K + j] = df_from(i == j ? 1.0f : 0.0f);
+    }
     __syncthreads();
 
-    // ---- 2. Cholesky of Sw with Mb carried along: L and G = L^-1 Mb ---------
+    // ---- 2. Cholesky of Sw with [Mb | I] carried along: L, G = L^-1 Mb, L^-1 -
     if (tid == 0) {
         const df d = sm.A[0][0];
         if (!(d.hi > static_cast<float>(PIVOT_REL) * sm.swd[0]) || !(d.hi > 0.0f)) {
@@ -261,15 +269,17 @@ __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm,
             sm.L[0][0] = df_mul(d, r);
         }
     }
+    const int KB = K + B;  // carried columns: Mb then the identity
     for (int j = 0; j < B; ++j) {
         __syncthreads();
         if (sm.fail) break;
-        // column j of L, row j of G, and the trailing update, in one phase:
-        // L[i][j] = A[i][j] r and G[j][c] = A[j][B + c] r are formed where used
+        // column j of L, row j of [G | L^-1], and the trailing update, in one
+        // phase: L[i][j] = A[i][j] r and the row-j entries are formed where used
         const df r = sm.invd[j];
         const int m = B - j - 1;
         const int ntri = m * (m + 1) / 2;
-        for (int e = tid; e < ntri + m * K + m + K; e += TPB) {
+        const int ncar = j + 1 + K;  // carried columns with nonzero row j: Mb and identity columns 0..j
+        for (int e = tid; e < ntri + m * ncar + m + ncar; e += TPB) {
             if (e < ntri) {
                 const int i = j + 1 + sm.tri_i[e], l = j + 1 + sm.tri_l[e];
                 const df v = df_fms(sm.A[i][l], df_mul(sm.A[i][j], r), df_mul(sm.A[l][j], r));
@@ -283,19 +293,23 @@ __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm,
                         sm.L[j + 1][j + 1] = df_mul(v, rr);
                     }
                 }
-            } else if (e < ntri + m * K) {
+            } else if (e < ntri + m * ncar) {
                 const int q = e - ntri;
-                const int i = j + 1 + q / K, c = q - (q / K) * K;
-                sm.A[i][B + c] = df_fms(sm.A[i][B + c], df_mul(sm.A[i][j], r), df_mul(sm.A[j][B + c], r));
-            } else if (e < ntri + m * K + m) {
-                const int i = j + 1 + (e - ntri - m * K);
+                const int i = j + 1 + q / ncar, cc = q - (q / ncar) * ncar;
+                const int col = B + cc;  // Mb columns, then identity columns 0..j
+                sm.A[i][col] = df_fms(sm.A[i][col], df_mul(sm.A[i][j], r), df_mul(sm.A[j][col], r));
+            } else if (e < ntri + m * ncar + m) {
+                const int i = j + 1 + (e - ntri - m * ncar);
                 sm.L[i][j] = df_mul(sm.A[i][j], r);
             } else {
-                const int c = e - ntri - m * K - m;
-                sm.G[j][c] = df_mul(sm.A[j][B + c], r);
+                const int cc = e - ntri - m * ncar - m;
+                const df v = df_mul(sm.A[j][B + cc], r);
+                if (cc < K) sm.G[j][cc] = v;
+                else sm.Li[j][cc - K] = v;
             }
         }
     }
+    (void)KB;
     __syncthreads();
     if (sm.fail) {
         if (tid == 0) set_status(dm, sm.fail);
@@ -372,10 +386,12 @@ __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm,
                     if (q < K) {
                         const float apq = sm.Tf[p][q];
                         if (apq != 0.0f) {
-                            const float tau = (sm.Tf[q][q] - sm.Tf[p][p]) / (2.0f * apq);
+                            // approximate intrinsics suffice: the refinement below
+                            // restores accuracy, only orthogonal-enough rotations matter
+                            const float tau = __fdividef(sm.Tf[q][q] - sm.Tf[p][p], 2.0f * apq);
                             float t;
-                            if (fabsf(tau) > 1e15f) t = 0.5f / tau;
-                            else t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+                            if (fabsf(tau) > 1e15f) t = __fdividef(0.5f, tau);
+                            else t = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.0f))), tau);
                             cs = rsqrtf(fmaf(t, t, 1.0f));
                             sn = t * cs;
                             ok = 1;
@@ -418,6 +434,7 @@ __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm,
         for (int e = lane; e < K * K; e += 32) sm.W[e / K][e % K] = df_from(sm.Wf[e / K][e % K]);
         __syncwarp();
         for (int it = 0; it < REFINE_STEPS; ++it) {
+            float emax = 0.0f;
             for (int e = lane; e < K * K; e += 32) {
                 const int a = e / K, b = e % K;
                 df r = df_from(0.0f), tw = df_from(0.0f);
@@ -462,7 +479,9 @@ __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm,
                     ev = df_from(num.hi / gap.hi);
                 }
                 sm.E[a][b] = ev;
+                emax = fmaxf(emax, fabsf(ev.hi));
             }
+            for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, o));
             __syncwarp();
             for (int e = lane; e < K * K; e += 32) {
                 const int a = e / K, b = e % K;
@@ -473,6 +492,7 @@ __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm,
             __syncwarp();
             for (int e = lane; e < K * K; e += 32) sm.W[e / K][e % K] = df_add(sm.W[e / K][e % K], sm.TW[e / K][e % K]);
             __syncwarp();
+            if (emax < 1e-6f) break;  // the next correction would be below the double-float rounding
         }
     }
     __syncthreads();
@@ -513,19 +533,21 @@ __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm,
     if (nv > r) complete_basis(sm, B, r, nv);
     const int ncols = nv;
 
-    // ---- 7. V = L^-T U: back substitution, one barrier per row -----------------
-    for (int e = tid; e < B * ncols; e += TPB) {
-        const int b = e / ncols, j = e - (e / ncols) * ncols;
-        sm.A[b][j] = sm.U[b][j];
-        if (b == B - 1) sm.V[b][j] = df_mul(sm.U[b][j], sm.invd[b]);
-    }
-    for (int i = B - 1; i > 0; --i) {
-        __syncthreads();
-        for (int e = tid; e < i * ncols; e += TPB) {
-            const int l = e / ncols, j = e - (e / ncols) * ncols;
-            const df v = df_fms(sm.A[l][j], sm.L[i][l], sm.V[i][j]);
-            sm.A[l][j] = v;
-            if (l == i - 1) sm.V[l][j] = df_mul(v, sm.invd[l]);
+    // ---- 7. V = L^-T U: each entry a split dot product over 8 lanes ---------
+    {
+        // the loop bound is a multiple of the block size, so every lane of a
+        // warp takes part in every shuffle
+        const int total = B * ncols * 8;
+        const int bound = (total + TPB - 1) / TPB * TPB;
+        for (int e = tid; e < bound; e += TPB) {
+            const bool live = e < total;
+            const int o = live ? (e >> 3) : 0, part = e & 7;
+            const int b = o / ncols, j = o - (o / ncols) * ncols;
+            df s8 = df_from(0.0f);
+            if (live)
+                for (int i = b + part; i < B; i += 8) s8 = df_fma(s8, sm.Li[i][b], sm.U[i][j]);  // (L^-1)^T[b][i] = Li[i][b]
+            for (int o2 = 4; o2 > 0; o2 >>= 1) s8 = df_add(s8, shfl_xor_df(s8, o2));
+            if (live && part == 0) sm.V[b][j] = s8;
         }
     }
     __syncthreads();

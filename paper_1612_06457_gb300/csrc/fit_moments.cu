@@ -10,27 +10,26 @@
 // though thread blocks merge their partial sums with atomics.
 //
 // Four kernels; the label map is cut into tiles of 16384 labels, one CTA per
-// tile in the two label passes (each thread holds 64 labels from four
-// 128-bit loads in flight):
+// tile in the label passes (each thread holds 64 labels from four 128-bit
+// loads in flight, compared four bytes at a time):
 //   k_tile_count    training pixels of each class in the tile, and whether
-//                   the tile holds a label above K (no global atomics);
-//   k_tile_scan     one CTA: prefix sums of the tile counts class by class,
-//                   giving each tile its first row in every class segment of
-//                   the class-major training matrix; class totals, the fit's
-//                   status word, and the reset of the moment accumulators;
-//   k_tile_gather   re-reads the tile, places every training pixel in its
-//                   class segment (block-wide scan of packed per-thread class
-//                   counts), and gathers its bands, one pixel per thread with
-//                   all band loads in flight, into the augmented row
-//                   (x_0 .. x_{B-1}, 1, 0 ..) of the training matrix;
-//   k_moments       walks the training matrix in units of up to 256 rows of
-//                   one class, staged in shared memory with 16-byte loads,
-//                   and accumulates exact products, each thread owning one
-//                   4x4 block of the upper triangle of x' x'^T and a stride
-//                   of the unit's rows.  Sums stay in registers while a CTA
-//                   stays on one class and are merged (shared memory, then
-//                   global 64-bit atomics) when it moves on.  The "1" column
-//                   yields n_c and s_c in the same loop.
+//                   the tile holds a label above K; the last CTA to finish
+//                   (atomic ticket, no waiting) then takes the prefix sums of
+//                   the tile counts class by class, giving each tile its
+//                   first row in every class segment of the class-major
+//                   training list, and writes the class totals, the fit's
+//                   status word and the reset of the moment accumulators;
+//   k_tile_compact  re-reads the tile and writes the pixel index of every
+//                   training pixel to its row of the class-major list
+//                   (block-wide scan of packed per-thread class counts);
+//   k_gather        one thread per listed pixel, all band loads in flight:
+//                   the augmented row (x_0 .. x_{B-1}, 1, 0 ..) of the
+//                   class-major training matrix (16-byte rows);
+//   k_moments       exact moments on the tensor cores, in units of up to 256
+//                   rows of one class (see the kernel).  Sums stay in
+//                   registers while a CTA stays on one class and are merged
+//                   into the model with 64-bit integer atomics when it moves
+//                   on.  The "1" column yields n_c and s_c in the same pass.
 #include "cva_internal.cuh"
 
 namespace cva {
@@ -42,8 +41,6 @@ constexpr int TILE = LABEL_TILE;   // 16384 = TPB * 64
 constexpr int SUB = TPB * 16;      // 4096 labels: one 128-bit load per thread
 constexpr int UNIT = 256;          // rows per work unit of the moments pass
 constexpr int NW = TPB / 32;
-constexpr int LIST = 4096;         // staged training pixels per gather round
-constexpr int SCAN_TPB = 1024;
 
 // The tile's 64 labels of this thread: four 16-byte groups, SUB apart.
 __device__ inline void load_tile(const uint8_t* __restrict__ labels, long long t0, long long P, int vec,
@@ -73,19 +70,6 @@ __device__ inline uint32_t byte_at(unsigned long long lo, unsigned long long hi,
     return static_cast<uint32_t>(((i < 8 ? lo : hi) >> (8 * (i & 7))) & 0xFFull);
 }
 
-// Bit i set when label byte i is a training label (1..K); `bad` when a label exceeds K.
-__device__ inline uint32_t train_mask(unsigned long long lo, unsigned long long hi, int K, int& bad)
-{
-    uint32_t m = 0;
-    #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const uint32_t l = byte_at(lo, hi, i);
-        m |= (l != 0u && l <= static_cast<uint32_t>(K)) ? (1u << i) : 0u;
-        bad |= (l > static_cast<uint32_t>(K)) ? 1 : 0;
-    }
-    return m;
-}
-
 // Class counters packed four to a 64-bit word (16-bit fields; a tile holds
 // 16384 labels, so no field carries into the next).
 __device__ inline unsigned int field(const unsigned long long (&v)[4], int c)
@@ -101,15 +85,6 @@ __device__ inline void bump(unsigned long long (&v)[4], int c)
     else if (c < 8) v[1] += one;
     else if (c < 12) v[2] += one;
     else v[3] += one;
-}
-
-__device__ inline unsigned int field_sum(const unsigned long long (&v)[4], int K)
-{
-    unsigned int s = 0;
-    #pragma unroll
-    for (int c = 0; c < MAXK; ++c)
-        if (c < K) s += field(v, c);
-    return s;
 }
 
 // Block-wide exclusive scan of packed counters (`nwords` words used).
@@ -152,24 +127,109 @@ __device__ inline void block_scan_packed(const unsigned long long (&cnt)[4], int
     }
 }
 
+// Four bits, one per byte of `r` (each byte 0x00 or 0xFF): bit i from byte i.
+__device__ inline uint32_t byte_bits(uint32_t r)
+{
+    const uint32_t t = r & 0x01010101u;
+    return (t | (t >> 7) | (t >> 14) | (t >> 21)) & 0xFu;
+}
+
+// Per-class counts of 16 labels (4 words) added into 16-bit fields, four
+// classes per 64-bit word; byte compares four at a time.
+__device__ inline void count16(const uint32_t (&w)[4], int K, unsigned long long (&cnt)[4])
+{
+    #pragma unroll
+    for (int c = 0; c < MAXK; ++c) {
+        if (c < K) {
+            const uint32_t pat = static_cast<uint32_t>(c + 1) * 0x01010101u;
+            uint32_t n = 0;
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) n += __popc(__vcmpeq4(w[q], pat) & 0x01010101u);
+            const unsigned long long add = static_cast<unsigned long long>(n) << (16 * (c & 3));
+            if (c < 4) cnt[0] += add; else if (c < 8) cnt[1] += add; else if (c < 12) cnt[2] += add; else cnt[3] += add;
+        }
+    }
+}
+
+// Prefix sums of the per-tile class counts, class by class (run by one CTA):
+// each tile's count row becomes its first row in every class segment of the
+// class-major training list.  Also the class totals, the fit's status word and
+// the reset of the moment accumulators.
+__device__ void scan_tiles(int ntiles, int K, int B, long long cap, int any_bad, unsigned int* __restrict__ tiles,
+                           DevModel* __restrict__ dm)
+{
+    __shared__ unsigned int woff[NW];
+    __shared__ unsigned int start;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (ntiles + TPB - 1) / TPB;
+    const int t_lo = min(ntiles, tid * per), t_hi = min(ntiles, t_lo + per);
+    if (tid == 0) start = 0u;
+    for (int c = 0; c < K; ++c) {
+        unsigned int acc = 0;
+        for (int t = t_lo; t < t_hi; ++t) acc += __ldcg(tiles + static_cast<long long>(t) * (K + 1) + c);
+        unsigned int v = acc;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane == 31) woff[warp] = v;
+        __syncthreads();
+        unsigned int before = 0, all = 0;
+        #pragma unroll
+        for (int w2 = 0; w2 < NW; ++w2) {
+            before += (w2 < warp) ? woff[w2] : 0u;
+            all += woff[w2];
+        }
+        unsigned int run = start + before + v - acc;
+        for (int t = t_lo; t < t_hi; ++t) {
+            unsigned int* cell = tiles + static_cast<long long>(t) * (K + 1) + c;
+            const unsigned int n = __ldcg(cell);
+            *cell = run;
+            run += n;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            dm->cls_count[c] = all;
+            start += all;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        int st = CVA_OK;
+        if (any_bad) st = CVA_ERR_LABEL_RANGE;
+        else if (static_cast<unsigned long long>(start) > static_cast<unsigned long long>(cap)) st = CVA_ERR_CAPACITY;
+        dm->status = st;
+        dm->fitted = 0;
+        dm->tile_ticket = 0u;
+    }
+    const MomShape sh = mom_shape(B);
+    for (int i = tid; i < K * sh.nblk * 16; i += TPB) {
+        const int c = i / (sh.nblk * 16), rest = i - c * sh.nblk * 16;
+        dm->mom[c][rest >> 4][rest & 15] = 0ull;
+    }
+}
+
 __global__ void __launch_bounds__(TPB)
-k_tile_count(const uint8_t* __restrict__ labels, long long P, int K, int vec, unsigned int* __restrict__ tiles)
+k_tile_count(const uint8_t* __restrict__ labels, long long P, int K, int B, int vec, long long cap, int ntiles,
+             unsigned int* __restrict__ tiles, DevModel* __restrict__ dm)
 {
     __shared__ unsigned long long wsum[NW][4];
     __shared__ int bad;
+    __shared__ int last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) bad = 0;
     uint32_t w[4][4];
     load_tile(labels, static_cast<long long>(blockIdx.x) * TILE, P, vec, w);
     unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
-    int my_bad = 0;
+    const uint32_t kpat = static_cast<uint32_t>(K) * 0x01010101u;
+    uint32_t over = 0;
     #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const unsigned long long l64 = w[u][0] | (static_cast<unsigned long long>(w[u][1]) << 32);
-        const unsigned long long h64 = w[u][2] | (static_cast<unsigned long long>(w[u][3]) << 32);
-        if ((l64 | h64) == 0ull) continue;
-        for (uint32_t m = train_mask(l64, h64, K, my_bad); m; m &= m - 1)
-            bump(cnt, static_cast<int>(byte_at(l64, h64, __ffs(m) - 1)) - 1);
+        if ((w[u][0] | w[u][1] | w[u][2] | w[u][3]) == 0u) continue;
+        count16(w[u], K, cnt);
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) over |= __vcmpgtu4(w[u][q], kpat);
     }
     #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -178,8 +238,8 @@ k_tile_count(const uint8_t* __restrict__ labels, long long P, int K, int vec, un
         #pragma unroll
         for (int q = 0; q < 4; ++q) wsum[warp][q] = cnt[q];
     }
-    __syncthreads();  // also orders the bad-flag reset before the writes below
-    if (my_bad) bad = 1;
+    __syncthreads();  // also orders the bad-flag reset before the update below
+    if (over) bad = 1;
     __syncthreads();
     if (tid <= K) {
         unsigned int v;
@@ -195,192 +255,156 @@ k_tile_count(const uint8_t* __restrict__ labels, long long P, int K, int vec, un
         }
         tiles[static_cast<long long>(blockIdx.x) * (K + 1) + tid] = v;
     }
-}
-
-__global__ void __launch_bounds__(SCAN_TPB)
-k_tile_scan(int ntiles, int K, int B, long long cap, unsigned int* __restrict__ tiles, DevModel* __restrict__ dm)
-{
-    constexpr int SW = SCAN_TPB / 32;
-    __shared__ unsigned int woff[SW][MAXK];
-    __shared__ unsigned int start[MAXK];
-    __shared__ int sbad;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (ntiles + SCAN_TPB - 1) / SCAN_TPB;
-    const int t_lo = min(ntiles, tid * per), t_hi = min(ntiles, t_lo + per);
-    if (tid == 0) sbad = 0;
-    unsigned int acc[MAXK];
-    #pragma unroll
-    for (int c = 0; c < MAXK; ++c) acc[c] = 0u;
-    int bad = 0;
-    for (int t = t_lo; t < t_hi; ++t) {
-        const unsigned int* row = tiles + static_cast<long long>(t) * (K + 1);
-        #pragma unroll
-        for (int c = 0; c < MAXK; ++c)
-            if (c < K) acc[c] += row[c];
-        bad |= row[K] != 0u;
-    }
-    // exclusive scan over threads, class by class
-    unsigned int ex[MAXK];
-    #pragma unroll
-    for (int c = 0; c < MAXK; ++c) {
-        if (c < K) {
-            unsigned int v = acc[c];
-            #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned int u = __shfl_up_sync(0xFFFFFFFFu, v, o);
-                if (lane >= o) v += u;
-            }
-            ex[c] = v - acc[c];
-            if (lane == 31) woff[warp][c] = v;
-        } else {
-            ex[c] = 0u;
-        }
-    }
-    __syncthreads();  // also orders the bad-flag reset before the update below
-    if (bad) sbad = 1;
-    if (tid < K) {
-        unsigned int run = 0;
-        for (int w2 = 0; w2 < SW; ++w2) {
-            const unsigned int v = woff[w2][tid];
-            woff[w2][tid] = run;
-            run += v;
-        }
-        dm->cls_count[tid] = run;
-        start[tid] = run;  // class total for now
-    }
+    // the last CTA to finish (atomic ticket after a fence) scans the counts;
+    // no CTA ever waits for another
+    __threadfence();
     __syncthreads();
-    if (tid == 0) {
-        unsigned long long tot = 0;
-        for (int c = 0; c < K; ++c) {
-            const unsigned int n = start[c];
-            start[c] = static_cast<unsigned int>(tot);
-            tot += n;
-        }
-        int st = CVA_OK;
-        if (sbad) st = CVA_ERR_LABEL_RANGE;
-        else if (tot > static_cast<unsigned long long>(cap)) st = CVA_ERR_CAPACITY;
-        dm->status = st;
-        dm->fitted = 0;
-    }
+    if (tid == 0) last = (atomicAdd(&dm->tile_ticket, 1u) == static_cast<unsigned int>(ntiles - 1));
     __syncthreads();
-    // each tile's first row in every class segment (in place of its counts)
-    unsigned int run[MAXK];
-    #pragma unroll
-    for (int c = 0; c < MAXK; ++c) run[c] = (c < K) ? start[c] + woff[warp][c] + ex[c] : 0u;
-    for (int t = t_lo; t < t_hi; ++t) {
-        unsigned int* row = tiles + static_cast<long long>(t) * (K + 1);
-        #pragma unroll
-        for (int c = 0; c < MAXK; ++c) {
-            if (c < K) {
-                const unsigned int n = row[c];
-                row[c] = run[c];
-                run[c] += n;
-            }
-        }
-    }
-    // reset the moment accumulators of this fit
-    const MomShape sh = mom_shape(B);
-    for (int i = tid; i < K * sh.nblk * 16; i += SCAN_TPB) {
-        const int c = i / (sh.nblk * 16), rest = i - c * sh.nblk * 16;
-        dm->mom[c][rest >> 4][rest & 15] = 0ull;
-    }
+    if (!last) return;
+    __threadfence();
+    int any_bad = 0;
+    for (int t = tid; t < ntiles; t += TPB) any_bad |= __ldcg(tiles + static_cast<long long>(t) * (K + 1) + K) != 0u;
+    any_bad = __syncthreads_or(any_bad);
+    scan_tiles(ntiles, K, B, cap, any_bad, tiles, dm);
 }
 
 __global__ void __launch_bounds__(TPB)
-k_tile_gather(const uint16_t* __restrict__ cube, int B, long long P, const uint8_t* __restrict__ labels, int K,
-              int vec, const unsigned int* __restrict__ tiles, uint16_t* __restrict__ xtr,
-              const DevModel* __restrict__ dm)
+k_tile_compact(const uint8_t* __restrict__ labels, long long P, int K, int vec,
+               const unsigned int* __restrict__ tiles, unsigned int* __restrict__ list,
+               const DevModel* __restrict__ dm)
 {
     __shared__ unsigned long long wsum[NW][4];
     __shared__ unsigned int base[MAXK];
-    __shared__ unsigned int lp[LIST], lr[LIST];
-    __shared__ int nlist;
     const int tid = threadIdx.x;
     if (dm->status != 0) return;
     const long long t0 = static_cast<long long>(blockIdx.x) * TILE;
     uint32_t w[4][4];
     load_tile(labels, t0, P, vec, w);
     if (tid < K) base[tid] = tiles[static_cast<long long>(blockIdx.x) * (K + 1) + tid];
-    if (tid == 0) nlist = 0;
-    const int nwords = (K + 3) >> 2;
-    const int BR = xtr_row(B);
-
-    auto gather = [&](int n) {
-        for (int i = tid; i < n; i += TPB) {
-            const uint16_t* src = cube + lp[i];
-            uint32_t xv[MAXB];
-            #pragma unroll
-            for (int b = 0; b < MAXB; ++b) xv[b] = (b < B) ? static_cast<uint32_t>(__ldg(src + static_cast<long long>(b) * P)) : 0u;
-            uint4* grow = reinterpret_cast<uint4*>(xtr + static_cast<long long>(lr[i]) * BR);
-            #pragma unroll
-            for (int q = 0; q < (MAXB + 8) / 8; ++q) {
-                if (q * 8 < BR) {
-                    uint32_t pk[4];
-                    #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int b0 = q * 8 + 2 * h, b1 = b0 + 1;
-                        const uint32_t v0 = (b0 < B) ? xv[b0 < MAXB ? b0 : 0] : (b0 == B ? 1u : 0u);
-                        const uint32_t v1 = (b1 < B) ? xv[b1 < MAXB ? b1 : 0] : (b1 == B ? 1u : 0u);
-                        pk[h] = v0 | (v1 << 16);
-                    }
-                    grow[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                }
-            }
-        }
-    };
-
-    int bad_unused = 0;
+    const uint32_t kpat = static_cast<uint32_t>(K) * 0x01010101u;
+    // training-label masks (nonzero and <= K) and per-class counts of the 64 labels
+    uint32_t mask[4];
+    unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
     #pragma unroll
     for (int u = 0; u < 4; ++u) {
+        mask[u] = 0u;
+        if ((w[u][0] | w[u][1] | w[u][2] | w[u][3]) != 0u) {
+            #pragma unroll
+            for (int q = 0; q < 4; ++q)
+                mask[u] |= byte_bits(~__vcmpeq4(w[u][q], 0u) & ~__vcmpgtu4(w[u][q], kpat)) << (4 * q);
+            count16(w[u], K, cnt);
+        }
+    }
+    unsigned long long excl[4], total[4];
+    block_scan_packed(cnt, (K + 3) >> 2, wsum, excl, total);  // also orders base[] before its reads
+    #pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if (!mask[u]) continue;
         const unsigned long long l64 = w[u][0] | (static_cast<unsigned long long>(w[u][1]) << 32);
         const unsigned long long h64 = w[u][2] | (static_cast<unsigned long long>(w[u][3]) << 32);
-        const uint32_t mask = (l64 | h64) ? train_mask(l64, h64, K, bad_unused) : 0u;
-        if (!__syncthreads_or(mask != 0u)) continue;
-        unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
-        for (uint32_t m = mask; m; m &= m - 1) bump(cnt, static_cast<int>(byte_at(l64, h64, __ffs(m) - 1)) - 1);
-        unsigned long long excl[4], total[4];
-        block_scan_packed(cnt, nwords, wsum, excl, total);
-        const unsigned int sub_n = field_sum(total, K);
-        if (nlist + static_cast<int>(sub_n) > LIST) {  // uniform: make room first
-            gather(nlist);
-            __syncthreads();
-            if (tid == 0) nlist = 0;
-            __syncthreads();
-        }
-        // slot in the staging list: pixels of this thread after those of lower threads
-        unsigned int slot = static_cast<unsigned int>(nlist) + field_sum(excl, K);
-        unsigned long long run[4] = {excl[0], excl[1], excl[2], excl[3]};
         const long long p0 = t0 + u * SUB + 16LL * tid;
-        for (uint32_t m = mask; m; m &= m - 1) {
+        for (uint32_t m = mask[u]; m; m &= m - 1) {
             const int i = __ffs(m) - 1;
             const int c = static_cast<int>(byte_at(l64, h64, i)) - 1;
-            lp[slot] = static_cast<unsigned int>(p0 + i);
-            lr[slot] = base[c] + field(run, c);
-            bump(run, c);
-            ++slot;
+            list[base[c] + field(excl, c)] = static_cast<unsigned int>(p0 + i);
+            bump(excl, c);
         }
-        __syncthreads();
-        if (tid < K) base[tid] += field(total, tid);
-        if (tid == 0) nlist += static_cast<int>(sub_n);
-        __syncthreads();
     }
-    gather(nlist);
 }
 
+// One thread per listed training pixel, all its band loads in flight: the
+// augmented row (x_0 .. x_{B-1}, 1, 0 ..) of the class-major training matrix.
+__global__ void __launch_bounds__(TPB)
+k_gather(const uint16_t* __restrict__ cube, int B, long long P, int K, const unsigned int* __restrict__ list,
+         uint16_t* __restrict__ xtr, const DevModel* __restrict__ dm)
+{
+    if (dm->status != 0) return;
+    unsigned int N = 0;
+    for (int c = 0; c < K; ++c) N += dm->cls_count[c];
+    const int BR = xtr_row(B);
+    const unsigned int stride = gridDim.x * TPB;
+    for (unsigned int i = blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
+        const uint16_t* src = cube + list[i];
+        uint32_t xv[MAXB];
+        #pragma unroll
+        for (int b = 0; b < MAXB; ++b) xv[b] = (b < B) ? static_cast<uint32_t>(__ldg(src + static_cast<long long>(b) * P)) : 0u;
+        uint4* grow = reinterpret_cast<uint4*>(xtr + static_cast<long long>(i) * BR);
+        #pragma unroll
+        for (int q = 0; q < (MAXB + 8) / 8; ++q) {
+            if (q * 8 < BR) {
+                uint32_t pk[4];
+                #pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int b0 = q * 8 + 2 * h, b1 = b0 + 1;
+                    const uint32_t v0 = (b0 < B) ? xv[b0 < MAXB ? b0 : 0] : (b0 == B ? 1u : 0u);
+                    const uint32_t v1 = (b1 < B) ? xv[b1 < MAXB ? b1 : 0] : (b1 == B ? 1u : 0u);
+                    pk[h] = v0 | (v1 << 16);
+                }
+                grow[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+    }
+}
+
+// ldmatrix / mma.sync wrappers (bf16 inputs, f32 accumulators)
+__device__ inline void ldsm_x4(uint32_t (&r)[4], const void* smem)
+{
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+
+__device__ inline void ldsm_x2(uint32_t (&r)[2], const void* smem)
+{
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+
+__device__ inline void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// bf16 bit pattern of an integer 0 <= v < 256 (exact: at most 8 significant bits).
+__device__ inline uint32_t bf16_of_byte(uint32_t v)
+{
+    return __float_as_uint(static_cast<float>(v)) >> 16;
+}
+
+constexpr int UPAD = UNIT + 8;  // shared row stride (bf16) of the transposed unit: conflict-free ldmatrix
+constexpr int MAXPAIR = MAXBA * (MAXBA + 1) / 2;
+
+// Exact moments on the tensor cores.  A unit holds up to 256 training rows of
+// one class.  Every 16-bit value x is split into its high and low bytes,
+// x = 256 h + l, both exact in bf16; the unit is stored transposed in shared
+// memory as the (2 F) x 256 matrix [h ; l] (F = padded augmented width), and
+// mma.sync forms its Gram matrix C = [h ; l] [h ; l]^T with FP32 accumulation.
+// Every partial sum is an integer below 256 * 255^2 < 2^24, so C is exact, and
+//     sum x_a x_b = 65536 C_hh[a][b] + 256 (C_hl[a][b] + C_lh[a][b]) + C_ll[a][b]
+// is recombined in 64-bit integers.  Each thread owns up to three (a <= b)
+// entries of the augmented moment matrix and keeps them in registers while
+// the CTA stays on one class.
 __global__ void __launch_bounds__(TPB)
 k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevModel* __restrict__ dm)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ unsigned int ustart[MAXK + 1], cstart[MAXK], ccount[MAXK];
-    __shared__ unsigned char sbi[MAXBLK], sbj[MAXBLK];
+    __shared__ unsigned char pa[MAXPAIR], pb[MAXPAIR];
     __shared__ int stop;
 
-    const MomShape sh = mom_shape(B);
-    const int BR = xtr_row(B);
-    const int tid = threadIdx.x;
-    const int G = TPB / sh.nblk;
-    uint16_t* X = reinterpret_cast<uint16_t*>(dyn);                                            // UNIT x BR
-    unsigned long long* part = reinterpret_cast<unsigned long long*>(dyn + UNIT * BR * 2);     // G x nblk x 16
+    const int F = xtr_row(B);       // padded augmented width (multiple of 8)
+    const int F2 = 2 * F;           // rows of the split matrix (multiple of 16)
+    const int BA = B + 1;
+    const int npair = BA * (BA + 1) / 2;
+    const int nb = mom_shape(B).nb;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint16_t* XT = reinterpret_cast<uint16_t*>(dyn);                     // F2 x UPAD bf16
+    float* Cs = reinterpret_cast<float*>(dyn + F2 * UPAD * 2);           // F2 x F2
 
     if (tid == 0) {
         unsigned int run = 0, units = 0;
@@ -397,41 +421,32 @@ k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevMode
         ustart[K] = units;
         stop = (dm->status != 0) || (tot > static_cast<unsigned long long>(cap));
     }
-    if (tid < sh.nblk) {
-        int idx = tid, bi = 0;
-        while (idx >= sh.nb - bi) { idx -= sh.nb - bi; ++bi; }
-        sbi[tid] = static_cast<unsigned char>(bi);
-        sbj[tid] = static_cast<unsigned char>(bi + idx);
-    }
+    for (int a = warp; a < BA; a += NW)
+        for (int b = a + lane; b < BA; b += 32) {
+            const int q = a * BA - a * (a - 1) / 2 + (b - a);
+            pa[q] = static_cast<unsigned char>(a);
+            pb[q] = static_cast<unsigned char>(b);
+        }
     __syncthreads();
     if (stop) return;
 
-    const int my_blk = tid % sh.nblk;
-    const int my_grp = tid / sh.nblk;
-    const bool worker = my_grp < G;
-    const int bi = worker ? sbi[my_blk] : 0, bj = worker ? sbj[my_blk] : 0;
-    unsigned long long a[16];
-    #pragma unroll
-    for (int q = 0; q < 16; ++q) a[q] = 0ull;
+    unsigned long long acc[3] = {0ull, 0ull, 0ull};
     int cur_class = -1;
+    const int MT = F2 / 16, NTL = F2 / 8;
 
     auto flush = [&](int c) {
-        if (worker) {
-            unsigned long long* dst = part + (my_grp * sh.nblk + my_blk) * 16;
-            #pragma unroll
-            for (int q = 0; q < 16; ++q) { dst[q] = a[q]; a[q] = 0ull; }
+        #pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int q = tid + k * TPB;
+            if (q < npair && acc[k]) {
+                const int a = pa[q], b = pb[q];
+                atomicAdd(&dm->mom[c][blk_index(a >> 2, b >> 2, nb)][(a & 3) * 4 + (b & 3)], acc[k]);
+            }
+            acc[k] = 0ull;
         }
-        __syncthreads();
-        for (int i = tid; i < sh.nblk * 16; i += TPB) {
-            unsigned long long v = 0ull;
-            for (int g = 0; g < G; ++g) v += part[g * sh.nblk * 16 + i];
-            if (v) atomicAdd(&dm->mom[c][i >> 4][i & 15], v);
-        }
-        __syncthreads();
     };
 
     const unsigned int nunits = ustart[K];
-    const int vec_per_row = BR / 8;
     for (unsigned int u = blockIdx.x; u < nunits; u += gridDim.x) {
         int c = 0;
         while (u >= ustart[c + 1]) ++c;
@@ -441,21 +456,56 @@ k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevMode
         }
         const unsigned int row0 = cstart[c] + (u - ustart[c]) * UNIT;
         const int len = static_cast<int>(min(static_cast<unsigned int>(UNIT), cstart[c] + ccount[c] - row0));
-        const uint4* src = reinterpret_cast<const uint4*>(xtr + static_cast<long long>(row0) * BR);
-        uint4* dst = reinterpret_cast<uint4*>(X);
-        for (int i = tid; i < len * vec_per_row; i += TPB) dst[i] = __ldg(src + i);
-        __syncthreads();
-        if (worker) {
-            for (int t = my_grp; t < len; t += G) {
-                const uint2 uu = *reinterpret_cast<const uint2*>(X + t * BR + 4 * bi);
-                const uint2 vv = *reinterpret_cast<const uint2*>(X + t * BR + 4 * bj);
-                const uint32_t xu[4] = {uu.x & 0xFFFFu, uu.x >> 16, uu.y & 0xFFFFu, uu.y >> 16};
-                const uint32_t xw[4] = {vv.x & 0xFFFFu, vv.x >> 16, vv.y & 0xFFFFu, vv.y >> 16};
-                #pragma unroll
-                for (int ia = 0; ia < 4; ++ia)
+        // split and transpose: thread tid owns pixel column tid of the unit
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(xtr + static_cast<long long>(row0 + tid) * F);
+            #pragma unroll
+            for (int q = 0; q < (MAXB + 8) / 8; ++q) {
+                if (q * 8 < F) {
+                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                    if (tid < len) v = __ldg(src + q);
+                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
                     #pragma unroll
-                    for (int ib = 0; ib < 4; ++ib)
-                        a[4 * ia + ib] += static_cast<unsigned long long>(xu[ia]) * xw[ib];
+                    for (int h = 0; h < 8; ++h) {
+                        const uint32_t x = (wv[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
+                        const int f = q * 8 + h;
+                        XT[f * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x >> 8));
+                        XT[(F + f) * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x & 0xFFu));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // Gram matrix of the split unit, one 16 x 8 output tile per warp at a time
+        for (int t = warp; t < MT * NTL; t += NW) {
+            const int mt = t / NTL, nt = t - (t / NTL) * NTL;
+            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            const uint16_t* arow = XT + (mt * 16 + (lane & 15)) * UPAD + ((lane >> 4) << 3);
+            const uint16_t* brow = XT + (nt * 8 + (lane & 7)) * UPAD + (((lane >> 3) & 1) << 3);
+            #pragma unroll 4
+            for (int ks = 0; ks < UNIT / 16; ++ks) {
+                uint32_t af[4], bfr[2];
+                ldsm_x4(af, arow + ks * 16);
+                ldsm_x2(bfr, brow + ks * 16);
+                mma_bf16_16816(d, af, bfr);
+            }
+            const int r0 = mt * 16 + (lane >> 2), c0 = nt * 8 + (lane & 3) * 2;
+            Cs[r0 * F2 + c0] = d[0];
+            Cs[r0 * F2 + c0 + 1] = d[1];
+            Cs[(r0 + 8) * F2 + c0] = d[2];
+            Cs[(r0 + 8) * F2 + c0 + 1] = d[3];
+        }
+        __syncthreads();
+        #pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int q = tid + k * TPB;
+            if (q < npair) {
+                const int a = pa[q], b = pb[q];
+                const unsigned long long hh = __float2uint_rn(Cs[a * F2 + b]);
+                const unsigned long long hl = __float2uint_rn(Cs[a * F2 + F + b]);
+                const unsigned long long lh = __float2uint_rn(Cs[(F + a) * F2 + b]);
+                const unsigned long long ll = __float2uint_rn(Cs[(F + a) * F2 + F + b]);
+                acc[k] += (hh << 16) + ((hl + lh) << 8) + ll;
             }
         }
         __syncthreads();
@@ -466,24 +516,24 @@ k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevMode
 }  // namespace
 
 cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const uint8_t* labels, int K,
-                               DevModel* dm, uint16_t* xtr, unsigned int* tiles, long long cap, int num_sms,
-                               cudaStream_t s)
+                               DevModel* dm, uint16_t* xtr, unsigned int* tiles, unsigned int* list, long long cap,
+                               int num_sms, cudaStream_t s)
 {
     const int vec = (reinterpret_cast<uintptr_t>(labels) % 16 == 0) ? 1 : 0;
     const long long ntiles = (P + TILE - 1) / TILE;
-    k_tile_count<<<static_cast<unsigned>(ntiles), TPB, 0, s>>>(labels, P, K, vec, tiles);
+    k_tile_count<<<static_cast<unsigned>(ntiles), TPB, 0, s>>>(labels, P, K, B, vec, cap, static_cast<int>(ntiles),
+                                                                 tiles, dm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_tile_scan<<<1, SCAN_TPB, 0, s>>>(static_cast<int>(ntiles), K, B, cap, tiles, dm);
+    k_tile_compact<<<static_cast<unsigned>(ntiles), TPB, 0, s>>>(labels, P, K, vec, tiles, list, dm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_tile_gather<<<static_cast<unsigned>(ntiles), TPB, 0, s>>>(cube, B, P, labels, K, vec, tiles, xtr, dm);
+    k_gather<<<static_cast<unsigned>(num_sms * 8), TPB, 0, s>>>(cube, B, P, K, list, xtr, dm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
-    const MomShape sh = mom_shape(B);
-    const int G = TPB / sh.nblk;
-    const size_t smem = static_cast<size_t>(UNIT) * xtr_row(B) * 2 + static_cast<size_t>(G) * sh.nblk * 16 * 8;
+    const int F2 = 2 * xtr_row(B);
+    const size_t smem = static_cast<size_t>(F2) * UPAD * 2 + static_cast<size_t>(F2) * F2 * 4;
     e = cudaFuncSetAttribute(k_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     // the unit count is only known on the device: size the grid for the
