@@ -167,14 +167,13 @@ __device__ inline float u16_biased(uint32_t x)
     return __int_as_float(static_cast<int>(0x4B000000u | x));
 }
 
-// 8-bit code of a projection value: floor((y - lo) * scale + 1/2) in 0..255.
-__device__ inline uint32_t to_code(float y, float lo, float scale)
+// 8-bit code of a projection value: floor(y * scale + off) clamped to 0..255,
+// with scale = 255 / (hi - lo) and off = 1/2 - lo * scale, i.e.
+// floor(255 (y - lo) / (hi - lo) + 1/2) up to FP32 rounding.
+__device__ inline uint32_t to_code(float y, float scale, float off)
 {
-    float t = __fmaf_rn(__fsub_rn(y, lo), scale, 0.5f);
-    int q = __float2int_rd(t);
-    q = q < 0 ? 0 : q;
-    q = q > 255 ? 255 : q;
-    return static_cast<uint32_t>(q);
+    const float t = fminf(fmaxf(__fmaf_rn(y, scale, off), 0.0f), 255.0f);
+    return static_cast<uint32_t>(__float2int_rd(t));
 }
 
 // The scale that maps [lo, hi] onto [0, 255]; 0 when the range is empty.
@@ -182,6 +181,12 @@ __device__ inline float code_scale(float lo, float hi)
 {
     float w = __fsub_rn(hi, lo);
     return (w > 0.0f && w < 3.0e38f) ? __fdiv_rn(255.0f, w) : 0.0f;
+}
+
+// The matching offset 1/2 - lo * scale.
+__device__ inline float code_offset(float lo, float scale)
+{
+    return __fmaf_rn(-lo, scale, 0.5f);
 }
 
 #endif  // __CUDACC__

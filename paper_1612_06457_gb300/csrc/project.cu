@@ -14,10 +14,12 @@
 // 8-bit code is floor((y - lo) * 255 / (hi - lo) + 1/2) clamped to 0..255.
 //
 // The pass is bound by HBM bandwidth (2B bytes in, k or 4k bytes out per
-// pixel): each thread streams 8 consecutive pixels per band with one 16-byte
-// evict-first load, keeps 8 x k FP32 accumulators in registers, and writes
-// 8-byte (u8) or 32-byte (f32) streaming stores.  A scalar kernel covers
-// pixel counts that are not a multiple of 8 and unaligned buffers.
+// pixel).  The main kernel (k_project_v8) gives each thread 8 consecutive
+// pixels, keeps 8 x k FP32 accumulators in registers, software-pipelines the
+// 16-byte band loads in batches of 8 so that up to 256 bytes per thread are
+// in flight, and writes 8-byte (u8) or 32-byte (f32) streaming stores.  A
+// scalar kernel covers pixel counts that are not a multiple of 8 and
+// unaligned buffers.
 //
 // The training-range kernel repeats the same FP32 operations, in the same
 // order, on the training pixels, so that the extreme training pixels land on
@@ -29,7 +31,6 @@ namespace cva {
 namespace {
 
 constexpr int TPB = 256;
-constexpr int PX = 8;    // pixels per thread per step in the vector path
 constexpr int KCH = 8;   // variates per pass
 constexpr int NWARP = TPB / 32;
 
@@ -38,7 +39,7 @@ struct ProjSmem {
     float V[MAXB][KV];
     float shift[MAXB];
     float d[KV];
-    float lo[KV];
+    float off[KV];
     float scale[KV];
     float mn[NWARP][KV];
     float mx[NWARP][KV];
@@ -61,28 +62,25 @@ __device__ inline void load_coefs(ProjSmem<KV>& sm, const DevModel* dm, int B, i
             lo = u8_range[2 * (j0 + tid)];
             hi = u8_range[2 * (j0 + tid) + 1];
         }
-        sm.lo[tid] = lo;
-        sm.scale[tid] = code_scale(lo, hi);
+        const float sc = code_scale(lo, hi);
+        sm.scale[tid] = sc;
+        sm.off[tid] = code_offset(lo, sc);
     }
 }
 
 template <int KV>
-__device__ inline void accumulate8(float (&acc)[KV][PX], const uint4& w, const float* vrow, float shift)
+__device__ inline void accumulate4(float (&acc)[KV][4], const uint2& w, const float* vrow, float shift)
 {
-    float x[PX];
+    float x[4];
     x[0] = __fsub_rn(u16_lo_biased(w.x), shift);
     x[1] = __fsub_rn(u16_hi_biased(w.x), shift);
     x[2] = __fsub_rn(u16_lo_biased(w.y), shift);
     x[3] = __fsub_rn(u16_hi_biased(w.y), shift);
-    x[4] = __fsub_rn(u16_lo_biased(w.z), shift);
-    x[5] = __fsub_rn(u16_hi_biased(w.z), shift);
-    x[6] = __fsub_rn(u16_lo_biased(w.w), shift);
-    x[7] = __fsub_rn(u16_hi_biased(w.w), shift);
     #pragma unroll
     for (int j = 0; j < KV; ++j) {
         const float v = vrow[j];
         #pragma unroll
-        for (int i = 0; i < PX; ++i) acc[j][i] = __fmaf_rn(v, x[i], acc[j][i]);
+        for (int i = 0; i < 4; ++i) acc[j][i] = __fmaf_rn(v, x[i], acc[j][i]);
     }
 }
 
@@ -115,9 +113,35 @@ __device__ inline void reduce_range(ProjSmem<KV>& sm, float (&mn)[KV], float (&m
     }
 }
 
-// Vector path: P % 8 == 0 and 16-byte aligned cube (and outputs).
+// ---------------------------------------------------------------------------
+// Register-pipelined streaming (P % 8 == 0, 16-byte aligned cube): each thread
+// takes 8 consecutive pixels and walks the bands in batches of 8 rows, the
+// 16-byte evict-first loads of the next batch issued before the current batch
+// is computed, so up to 16 loads (256 bytes) per thread stay in flight while
+// the coefficients in shared memory are reused for 8 pixels.
+// ---------------------------------------------------------------------------
+template <int KV>
+__device__ inline void accumulate8(float (&acc)[KV][8], const uint4& w, const float* vrow, float shift)
+{
+    float x[8];
+    x[0] = __fsub_rn(u16_lo_biased(w.x), shift);
+    x[1] = __fsub_rn(u16_hi_biased(w.x), shift);
+    x[2] = __fsub_rn(u16_lo_biased(w.y), shift);
+    x[3] = __fsub_rn(u16_hi_biased(w.y), shift);
+    x[4] = __fsub_rn(u16_lo_biased(w.z), shift);
+    x[5] = __fsub_rn(u16_hi_biased(w.z), shift);
+    x[6] = __fsub_rn(u16_lo_biased(w.w), shift);
+    x[7] = __fsub_rn(u16_hi_biased(w.w), shift);
+    #pragma unroll
+    for (int j = 0; j < KV; ++j) {
+        const float v = vrow[j];
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) acc[j][i] = __fmaf_rn(v, x[i], acc[j][i]);
+    }
+}
+
 template <int KV, bool F32, bool U8, bool RNG>
-__global__ void __launch_bounds__(TPB)
+__global__ void __launch_bounds__(TPB, 2)
 k_project_v8(const uint16_t* __restrict__ cube, int B, long long P, const DevModel* __restrict__ dm,
              int j0, const float* __restrict__ u8_range, float* __restrict__ out_f32,
              uint8_t* __restrict__ out_u8, float* __restrict__ range_acc)
@@ -131,50 +155,67 @@ k_project_v8(const uint16_t* __restrict__ cube, int B, long long P, const DevMod
     #pragma unroll
     for (int j = 0; j < KV; ++j) { mn[j] = __int_as_float(0x7F800000); mx[j] = __int_as_float(0xFF800000); }
 
-    const long long ngroups = P / PX;
+    const long long ngroups = P / 8;
+    const long long plane = P / 8;  // band stride in uint4 units
     const long long stride = static_cast<long long>(gridDim.x) * TPB;
     for (long long g = static_cast<long long>(blockIdx.x) * TPB + threadIdx.x; g < ngroups; g += stride) {
-        const long long p = g * PX;
-        float acc[KV][PX];
+        const uint4* src = reinterpret_cast<const uint4*>(cube) + g;
+        float acc[KV][8];
         #pragma unroll
         for (int j = 0; j < KV; ++j)
             #pragma unroll
-            for (int i = 0; i < PX; ++i) acc[j][i] = 0.0f;
-        const uint16_t* src = cube + p;
-        int b = 0;
-        for (; b + 4 <= B; b += 4) {
-            uint4 w[4];
+            for (int i = 0; i < 8; ++i) acc[j][i] = 0.0f;
+        uint4 wa[8], wb[8];
+        #pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (u < B) wa[u] = __ldcs(src + u * plane);
+        for (int b0 = 0;; b0 += 16) {
+            // the batch tests are the same for every thread: whole batches are
+            // skipped by branches, only a partial last batch is predicated
+            const bool second = b0 + 8 < B;
+            if (second) {
+                #pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (b0 + 8 + u < B) wb[u] = __ldcs(src + (b0 + 8 + u) * plane);
+            }
             #pragma unroll
-            for (int u = 0; u < 4; ++u) w[u] = __ldcs(reinterpret_cast<const uint4*>(src + static_cast<long long>(b + u) * P));
+            for (int u = 0; u < 8; ++u)
+                if (b0 + u < B) accumulate8<KV>(acc, wa[u], sm.V[b0 + u], sm.shift[b0 + u]);
+            if (!second) break;
+            const bool third = b0 + 16 < B;
+            if (third) {
+                #pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (b0 + 16 + u < B) wa[u] = __ldcs(src + (b0 + 16 + u) * plane);
+            }
             #pragma unroll
-            for (int u = 0; u < 4; ++u) accumulate8<KV>(acc, w[u], sm.V[b + u], sm.shift[b + u]);
+            for (int u = 0; u < 8; ++u)
+                if (b0 + 8 + u < B) accumulate8<KV>(acc, wb[u], sm.V[b0 + 8 + u], sm.shift[b0 + 8 + u]);
+            if (!third) break;
         }
-        for (; b < B; ++b) {
-            const uint4 w = __ldcs(reinterpret_cast<const uint4*>(src + static_cast<long long>(b) * P));
-            accumulate8<KV>(acc, w, sm.V[b], sm.shift[b]);
-        }
+        const long long p = g * 8;
         #pragma unroll
         for (int j = 0; j < KV; ++j) {
-            float y[PX];
+            float y[8];
             #pragma unroll
-            for (int i = 0; i < PX; ++i) y[i] = __fsub_rn(acc[j][i], sm.d[j]);
+            for (int i = 0; i < 8; ++i) y[i] = __fsub_rn(acc[j][i], sm.d[j]);
             if (F32) {
                 float4* dst = reinterpret_cast<float4*>(out_f32 + static_cast<long long>(j0 + j) * P + p);
                 __stcs(dst, make_float4(y[0], y[1], y[2], y[3]));
                 __stcs(dst + 1, make_float4(y[4], y[5], y[6], y[7]));
             }
             if (U8) {
-                const float lo = sm.lo[j], sc = sm.scale[j];
-                uint32_t c[PX];
+                const float sc = sm.scale[j], of = sm.off[j];
+                uint32_t c[8];
                 #pragma unroll
-                for (int i = 0; i < PX; ++i) c[i] = to_code(y[i], lo, sc);
+                for (int i = 0; i < 8; ++i) c[i] = to_code(y[i], sc, of);
                 const uint2 packed = make_uint2(c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24),
                                                 c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24));
                 __stcs(reinterpret_cast<uint2*>(out_u8 + static_cast<long long>(j0 + j) * P + p), packed);
             }
             if (RNG) {
                 #pragma unroll
-                for (int i = 0; i < PX; ++i) { mn[j] = fminf(mn[j], y[i]); mx[j] = fmaxf(mx[j], y[i]); }
+                for (int i = 0; i < 8; ++i) { mn[j] = fminf(mn[j], y[i]); mx[j] = fmaxf(mx[j], y[i]); }
             }
         }
     }
@@ -211,7 +252,7 @@ k_project_s(const uint16_t* __restrict__ cube, int B, long long P, long long p_b
             if (j >= kc) break;
             const float y = __fsub_rn(acc[j], sm.d[j]);
             if (F32) out_f32[static_cast<long long>(j0 + j) * P + p] = y;
-            if (U8) out_u8[static_cast<long long>(j0 + j) * P + p] = static_cast<uint8_t>(to_code(y, sm.lo[j], sm.scale[j]));
+            if (U8) out_u8[static_cast<long long>(j0 + j) * P + p] = static_cast<uint8_t>(to_code(y, sm.scale[j], sm.off[j]));
             if (RNG) { mn[j] = fminf(mn[j], y); mx[j] = fmaxf(mx[j], y); }
         }
     }
@@ -325,8 +366,8 @@ k_f32_to_u8(const float* __restrict__ proj, int k, long long P, int vec, const f
             uint8_t* __restrict__ out)
 {
     const int j = blockIdx.y;
-    const float lo = range[2 * j];
-    const float sc = code_scale(lo, range[2 * j + 1]);
+    const float sc = code_scale(range[2 * j], range[2 * j + 1]);
+    const float lo = code_offset(range[2 * j], sc);  // the code offset
     const float* src = proj + static_cast<long long>(j) * P;
     uint8_t* dst = out + static_cast<long long>(j) * P;
     const long long stride = static_cast<long long>(gridDim.x) * TPB;
@@ -336,13 +377,13 @@ k_f32_to_u8(const float* __restrict__ proj, int k, long long P, int vec, const f
         const long long n4 = P / 4;
         for (long long g = start; g < n4; g += stride) {
             const float4 v = __ldcs(reinterpret_cast<const float4*>(src) + g);
-            const uint32_t c = to_code(v.x, lo, sc) | (to_code(v.y, lo, sc) << 8) |
-                               (to_code(v.z, lo, sc) << 16) | (to_code(v.w, lo, sc) << 24);
+            const uint32_t c = to_code(v.x, sc, lo) | (to_code(v.y, sc, lo) << 8) |
+                               (to_code(v.z, sc, lo) << 16) | (to_code(v.w, sc, lo) << 24);
             __stcs(reinterpret_cast<unsigned int*>(dst) + g, c);
         }
         done = n4 * 4;
     }
-    for (long long p = done + start; p < P; p += stride) dst[p] = static_cast<uint8_t>(to_code(src[p], lo, sc));
+    for (long long p = done + start; p < P; p += stride) dst[p] = static_cast<uint8_t>(to_code(src[p], sc, lo));
 }
 
 template <int KV, bool F32, bool U8, bool RNG>
@@ -356,7 +397,7 @@ cudaError_t run_v8(const uint16_t* cube, int B, long long P, const DevModel* dm,
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    const long long ngroups = P / PX;
+    const long long ngroups = P / 8;
     long long grid = (ngroups + TPB - 1) / TPB;
     const long long cap = static_cast<long long>(num_sms) * per_sm;
     if (grid > cap) grid = cap;
@@ -385,8 +426,7 @@ cudaError_t run_chunk(const uint16_t* cube, int B, long long P, const DevModel* 
             default: e = run_v8<8, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s); break;
         }
         if (e != cudaSuccess) return e;
-        p_tail = (P / PX) * PX;
-        if (p_tail == P) return cudaSuccess;
+        return cudaSuccess;
     }
     long long n = P - p_tail;
     long long grid = (n + TPB - 1) / TPB;
@@ -432,9 +472,9 @@ cudaError_t launch_project(const uint16_t* cube, int B, long long P, const DevMo
                            float* out_f32, uint8_t* out_u8, const float* u8_range, float* range_acc,
                            int num_sms, cudaStream_t s)
 {
-    const bool aligned = (P % PX == 0) && (reinterpret_cast<uintptr_t>(cube) % 16 == 0) &&
+    const bool aligned = (P % 8 == 0) && (reinterpret_cast<uintptr_t>(cube) % 16 == 0) &&
                          (!out_f32 || reinterpret_cast<uintptr_t>(out_f32) % 16 == 0) &&
-                         (!out_u8 || reinterpret_cast<uintptr_t>(out_u8) % 8 == 0);
+                         (!out_u8 || reinterpret_cast<uintptr_t>(out_u8) % 4 == 0);
     const bool f32 = out_f32 != nullptr, u8 = out_u8 != nullptr, rng = range_acc != nullptr;
     for (int j0 = 0; j0 < k; j0 += KCH) {
         const int kc = (k - j0) < KCH ? (k - j0) : KCH;
