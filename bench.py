@@ -39,8 +39,8 @@ L2_BYTES = 126 * 1024 * 1024
 # DRAM traffic of one k_project_v8<3, u8> launch on the 23-band 4096 x 4096
 # cube, from ncu (dram__bytes_read.sum + dram__bytes_write.sum), valid while
 # the projection source hashes to PROJECT_SRC_SHA256; null otherwise.
-PROJECT_TRAFFIC_BYTES = None
-PROJECT_SRC_SHA256 = None
+PROJECT_TRAFFIC_BYTES = 771844608 + 34279168
+PROJECT_SRC_SHA256 = "f9659a058bae89b222aaf2c811a23a04fb1e0edc78f572a93faa6c0323dfcd67"
 
 
 def _args():
