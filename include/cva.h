@@ -175,6 +175,32 @@ int cva_to_u8(const float* proj, int k, int H, int W, int mode, const float* ran
 int cva_project_u8(const uint16_t* cube, int B, int H, int W, cva_model* m, int k, int mode,
                    const float* range, uint8_t* out, void* stream);
 
+/* Fit and fused projection to 8 bits in one call that allocates no device
+ * memory (the paper has no counterpart: this serves callers that cannot
+ * allocate, e.g. code running inside another framework's memory budget,
+ * application plug-ins that forbid device allocations after start-up, or
+ * loops that must never enter the driver's allocator).
+ * Does what cva_fit followed by cva_project_u8 with CVA_RANGE_TRAINING does
+ * (the same kernels), forming k canonical vectors.  All scratch memory (about
+ * 22 MB) is one array in the library's device data, which every GPU that
+ * loads the library holds until the process exits.
+ *   cube, labels  device, as for cva_fit
+ *   k             variates to project, 1 <= k <= B
+ *   out           device, k x H x W uint8
+ *   eigvals       device, B doubles, or NULL: the eigenvalues
+ *   status        device, one int, or NULL: CVA_OK or the device-side error
+ *                 of this call; on an error `out` is not written and
+ *                 `eigvals` holds no meaningful values
+ * Limits: H W <= 2^26 pixels (host check, CVA_ERR_INVALID_ARG) and at most
+ * 2^18 training pixels (device check, CVA_ERR_CAPACITY in *status).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race.  Calls are
+ * asynchronous on `stream`. */
+int cva_fit_project_u8_noalloc(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, int K,
+                               int k, uint8_t* out, double* eigvals, int* status, void* stream);
+
 /* Human-readable text of a CVA_* code (static storage). */
 const char* cva_strerror(int code);
 

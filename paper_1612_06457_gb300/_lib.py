@@ -53,6 +53,7 @@ SIGNATURES = {
     "cva_project": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P]),
     "cva_to_u8": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "cva_project_u8": (_I, [_P, _I, _I, _I, _P, _I, _I, _P, _P, _P]),
+    "cva_fit_project_u8_noalloc": (_I, [_P, _I, _I, _I, _P, _I, _I, _P, _P, _P, _P]),
     "cva_strerror": (ctypes.c_char_p, [_I]),
 }
 
@@ -225,3 +226,20 @@ def cva_project_u8(cube: torch.Tensor, m: Model, k: int, mode: int, out: torch.T
                                _dptr(range, torch.float32, "range"), _dptr(out, torch.uint8, "out"),
                                _stream_ptr(stream))
     _check(rc, "cva_project_u8")
+
+
+def cva_fit_project_u8_noalloc(cube: torch.Tensor, labels: torch.Tensor, K: int, k: int, out: torch.Tensor,
+                               eigvals: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
+                               stream=None) -> None:
+    """Fit and fused 8-bit projection without device allocations (see cva.h).
+    ``eigvals`` (float64, B) and ``status`` (int32, 1) are optional device
+    outputs."""
+    B, H, W = cube.shape
+    if tuple(labels.shape) != (H, W):
+        raise ValueError("labels must be H x W")
+    rc = load().cva_fit_project_u8_noalloc(_dptr(cube, torch.uint16, "cube"), B, H, W,
+                                           _dptr(labels, torch.uint8, "labels"), K, k,
+                                           _dptr(out, torch.uint8, "out"),
+                                           _dptr(eigvals, torch.float64, "eigvals"),
+                                           _dptr(status, torch.int32, "status"), _stream_ptr(stream))
+    _check(rc, "cva_fit_project_u8_noalloc")
