@@ -39,8 +39,8 @@ L2_BYTES = 126 * 1024 * 1024
 # DRAM traffic of one k_project_v8<3, u8> launch on the 23-band 4096 x 4096
 # cube, from ncu (dram__bytes_read.sum + dram__bytes_write.sum), valid while
 # the projection source hashes to PROJECT_SRC_SHA256; null otherwise.
-PROJECT_TRAFFIC_BYTES = 771844608 + 34279168
-PROJECT_SRC_SHA256 = "f9659a058bae89b222aaf2c811a23a04fb1e0edc78f572a93faa6c0323dfcd67"
+PROJECT_TRAFFIC_BYTES = 771805952 + 34662144
+PROJECT_SRC_SHA256 = "5cbc33dda6d8f3aac81f4edac25ef2979742118cd24f1a29626107d92cc7df71"
 
 
 def _args():
@@ -52,6 +52,7 @@ def _args():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP64-form comparison")
     return ap.parse_args()
 
 
@@ -143,9 +144,10 @@ class ClockSampler:
                 "power_w_max": max((num(r[3]) or 0) for r in loaded)}
 
 
-def _oracle_step_time(w, rows):
+def _oracle_step_time(w, rows, keep=None):
     """Oracle fit on the whole cube plus projection, training range and 8-bit
-    rescale of the first `rows` image rows; returns (t_fit, t_rows)."""
+    rescale of the first `rows` image rows; returns (t_fit, t_rows).  With a
+    dict `keep`, the oracle's fit, projection rows, range and codes go there."""
     import numpy as np
 
     import oracle
@@ -162,8 +164,10 @@ def _oracle_step_time(w, rows):
     t1 = time.perf_counter()
     p1 = rows * w.W
     y = oracle.project(w.cube, f["V"], f["mu"], w.k, 0, p1)
-    oracle.to_u8(y, rng)
+    u8 = oracle.to_u8(y, rng)
     t2 = time.perf_counter()
+    if keep is not None:
+        keep.update(fit=f, y=y, u8=u8, rows=rows)
     return t1 - t0, t2 - t1
 
 
@@ -195,6 +199,89 @@ def _config(w):
     return {"workload": w.name, "bands": w.B, "H": w.H, "W": w.W, "classes": w.K,
             "train_pixels": list(w.n_train), "variates": w.k, "range": "training-score (second rescale)",
             "l2": f"inputs larger than L2 ({(w.cube.nbytes + w.labels.nbytes) / 1e6:.0f} MB > {L2_BYTES / 2**20:.0f} MiB)"}
+
+
+def _time_graphs(torch, graphs, stream, steps):
+    with torch.cuda.stream(stream):
+        for g in graphs:
+            g.replay()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            for g in graphs:
+                g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _precision_forms(cva, torch, w, m, cube, labels, out, stream, steps=5):
+    """The FP64 form of the same step (CVA_PRECISION_FP64: FP64 training range,
+    FP64 projection and 8-bit codes) timed the same way, and the mixed form's
+    projections and codes against it over every pixel."""
+    P = w.P
+    y = {}
+    u = {}
+    res = {"bound": 1e-4}
+    for mode, name in ((cva.CVA_PRECISION_FP64, "fp64"), (cva.CVA_PRECISION_MIXED, "mixed")):
+        cva.cva_set_precision(m, mode)
+        g_fit = torch.cuda.CUDAGraph()
+        g_proj = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_fit, stream=stream):
+            cva.cva_fit(cube, labels, w.K, m, stream=stream)
+        with torch.cuda.graph(g_proj, stream=stream):
+            cva.cva_project_u8(cube, m, w.k, cva.CVA_RANGE_TRAINING, out, stream=stream)
+        t = _time_graphs(torch, (g_fit, g_proj), stream, steps)
+        res[name] = {"ms_per_step": t, "value": P / (t * 1e-3) / 1e6, "unit": UNIT, "steps": steps}
+        u[name] = out.clone()
+        yy = torch.empty((w.k, w.H, w.W), dtype=torch.float32, device=cube.device)
+        with torch.cuda.stream(stream):
+            cva.cva_project(cube, m, w.k, out_f32=yy, stream=stream)
+        torch.cuda.synchronize()
+        y[name] = yy.reshape(w.k, -1)
+    d = (y["mixed"] - y["fp64"]).abs().amax(dim=1) / y["fp64"].abs().amax(dim=1)
+    du = (u["mixed"].to(torch.int16) - u["fp64"].to(torch.int16)).abs()
+    res["mixed_vs_fp64"] = {"projection_rel_err_max": float(d.max().item()),
+                            "projection_rel_err_per_variate": [float(v) for v in d.tolist()],
+                            "u8_within_1": float((du <= 1).float().mean().item()),
+                            "u8_identical": float((du == 0).float().mean().item()),
+                            "pixels": P}
+    res["speedup_mixed_over_fp64"] = res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"]
+    cva.cva_set_precision(m, cva.CVA_PRECISION_MIXED)
+    with torch.cuda.stream(stream):
+        cva.cva_fit(cube, labels, w.K, m, stream=stream)
+        cva.cva_project_u8(cube, m, w.k, cva.CVA_RANGE_TRAINING, out, stream=stream)
+    torch.cuda.synchronize()
+    return res
+
+
+def _errors_vs_oracle(cva, torch, w, m, cube, out, keep, stream):
+    """Eigenvalues, canonical vectors (S_w norm), projections and codes of the
+    mixed form against the FP64 oracle (projection rows: the oracle's sample)."""
+    import numpy as np
+
+    f = keep["fit"]
+    lam, V, mu, _ = cva.cva_model_get(m, stream=stream)
+    r = min(w.K - 1, w.B)
+    lam_rel = np.abs(lam[:r] - f["lam"][:r]) / f["lam"][:r]
+    Sw = f["Sw"]
+    vs = [float(np.sqrt((V[:, j] - f["V"][:, j]) @ Sw @ (V[:, j] - f["V"][:, j]))) for j in range(min(r, w.k))]
+    p1 = keep["rows"] * w.W
+    yy = torch.empty((w.k, w.H, w.W), dtype=torch.float32, device=cube.device)
+    with torch.cuda.stream(stream):
+        cva.cva_project(cube, m, w.k, out_f32=yy, stream=stream)
+    torch.cuda.synchronize()
+    yg = yy.reshape(w.k, -1)[:, :p1].cpu().numpy().astype(np.float64)
+    yr = keep["y"]
+    rel = np.abs(yg - yr).max(axis=1) / np.abs(yr).max(axis=1)
+    ug = out.reshape(w.k, -1)[:, :p1].cpu().numpy().astype(np.int32)
+    du = np.abs(ug - keep["u8"].astype(np.int32))
+    return {"eigvals_rel_err": [float(v) for v in lam_rel], "eigvecs_sw_err": vs,
+            "projection_rel_err_max": float(rel.max()), "u8_within_1": float((du <= 1).mean()),
+            "u8_identical": float((du == 0).mean()), "pixels_compared": int(p1)}
 
 
 def run_ours(a):
@@ -323,6 +410,10 @@ def run_ours(a):
     if st != cva.CVA_OK:
         raise SystemExit(f"fit failed during timing: {cva.cva_strerror(st)}")
 
+    precision = None
+    if rank == 0 and not a.no_precision:
+        precision = _precision_forms(cva, torch, w, m, cube, labels, out, stream)
+
     if rank == 0:
         peak, peak_kind = _peaks()
         alg_bytes = P * (2 * w.B + w.k)
@@ -347,10 +438,15 @@ def run_ours(a):
             "gpu_launches": launches_per_step * a.steps,
             "clocks": clocks,
             "fit_ms": ms - proj_ms,
+            "precision": precision,
         }
         if not a.no_cpu_baseline and world == 1:
             rows = max(1, min(w.H, 256 * 4096 // max(w.W, 1)))
-            tf, tr = _oracle_step_time(w, rows)
+            keep = {}
+            tf, tr = _oracle_step_time(w, rows, keep)
+            errs = _errors_vs_oracle(cva, torch, w, m, cube, out, keep, stream)
+            if precision is not None:
+                precision["err_vs_oracle"] = errs
             t = tf + tr * (w.H / rows)
             line["cpu_baseline"] = {
                 "value": P / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -61,16 +61,22 @@ typedef enum {
     CVA_RANGE_GIVEN = 2     /* a caller-supplied range */
 } cva_range_mode;
 
-/* Arithmetic of the fit and the projection. */
+/* Arithmetic of the projection and of the training-score range.  The fit is
+ * the same in both: class moments from BF16 hi/lo split pixel values
+ * (x = 256 hi + lo, both exact in BF16) on the tensor cores with FP32
+ * accumulation, exact because every partial sum stays below 2^24 and is
+ * merged in 64-bit integers; scatter matrices rounded once to FP64;
+ * Cholesky, eigensolve and coefficients in double-float (about 48 bits) and
+ * published as FP64. */
 typedef enum {
-    /* Class moments in exact 64-bit integer arithmetic, FP64 scatter,
-     * eigensolve and coefficients, FP32 projection. */
-    CVA_PRECISION_EXACT = 0,
-    /* Class means first (exact), then the within-class scatter from BF16
-     * hi/lo split mean-shifted values on the tensor cores with FP32
-     * accumulation, merged in FP64; projection from BF16 hi/lo split
-     * operands on the tensor cores with FP32 accumulation. */
-    CVA_PRECISION_SPLIT_BF16 = 1
+    /* Default.  Projection in FP32: exact centring on the integer part of
+     * the mean, FP32 coefficients and accumulation.  HBM-bound. */
+    CVA_PRECISION_MIXED = 0,
+    /* Projection and training range with FP64 coefficients, centring and
+     * accumulation; 8-bit codes computed in FP64.  Bound by the FP64 pipe,
+     * several times slower; the plain form the mixed one is measured
+     * against.  cva_to_u8 is FP32 in both modes (its input is FP32). */
+    CVA_PRECISION_FP64 = 1
 } cva_precision_mode;
 
 typedef struct cva_model cva_model;
@@ -93,8 +99,10 @@ int cva_model_reserve(cva_model* m, int64_t max_train);
 /* Free the model (synchronizes the device first).  NULL is a no-op. */
 void cva_model_destroy(cva_model* m);
 
-/* Select CVA_PRECISION_EXACT (default) or CVA_PRECISION_SPLIT_BF16 for the
- * following fits and projections. */
+/* Select CVA_PRECISION_MIXED (default) or CVA_PRECISION_FP64 for the
+ * following calls.  May change between a fit and its projections: the FP64
+ * training range is formed by the fit in FP64 mode, else by the first call
+ * that needs it (from the fit's gathered training pixels).  Host-side only. */
 int cva_set_precision(cva_model* m, int mode);
 
 /* Number of canonical vectors, with their training-score ranges, that each
@@ -133,7 +141,8 @@ int cva_status(cva_model* m, void* stream);
  *                (columns j >= nvec, see cva_set_variates, are 0)
  *   mean         host, B doubles (mean of all training pixels)
  *   train_range  host, 2 B floats: training-score (lo, hi) of each variate
- *                (+inf, -inf for j >= nvec)
+ *                in the current precision mode (FP64 mode: rounded to
+ *                float); undefined for j >= nvec
  * Returns the model's device status, or CVA_ERR_NOT_FITTED. */
 int cva_model_get(cva_model* m, double* eigvals, double* V, double* mean, float* train_range,
                   void* stream);

@@ -31,8 +31,8 @@ CVA_RANGE_GLOBAL = 0
 CVA_RANGE_TRAINING = 1
 CVA_RANGE_GIVEN = 2
 
-CVA_PRECISION_EXACT = 0
-CVA_PRECISION_SPLIT_BF16 = 1
+CVA_PRECISION_MIXED = 0
+CVA_PRECISION_FP64 = 1
 
 CVA_MAX_BANDS = 32
 CVA_MAX_CLASSES = 16

@@ -16,6 +16,8 @@ struct cva_model {
     int num_sms;
     int nvec;
     int precision;
+    int fit_nvec;        // canonical vectors formed by the last fit
+    bool range64_valid;  // dm->train_enc64 belongs to the last fit
     cva::DevModel* dm;
     unsigned int* tiles; // per-tile class counts, then first rows (MAX_TILES x (K + 1))
     unsigned int* list;  // class-major training-pixel indices, cap entries
@@ -51,6 +53,16 @@ bool valid_dims(int B, int H, int W)
     if (B < 1 || B > CVA_MAX_BANDS || H < 1 || W < 1) return false;
     const long long P = static_cast<long long>(H) * W;
     return P < (1LL << 31);
+}
+
+// The FP64 training range of the last fit, formed on first use from the
+// gathered training matrix (which stays valid until the next fit).
+cudaError_t ensure_range64(cva_model* m, cudaStream_t s)
+{
+    if (m->range64_valid) return cudaSuccess;
+    const cudaError_t e = cva::launch_train_range64(m->B, m->K, m->xtr, m->dm, m->fit_nvec, m->num_sms, s);
+    if (e == cudaSuccess) m->range64_valid = true;
+    return e;
 }
 
 int read_status(cva_model* m, cudaStream_t s, int* fitted)
@@ -122,7 +134,9 @@ int cva_model_create(int B, int K, cva_model** out)
     m->device = dev;
     m->num_sms = sms;
     m->nvec = B;
-    m->precision = CVA_PRECISION_EXACT;
+    m->precision = CVA_PRECISION_MIXED;
+    m->fit_nvec = B;
+    m->range64_valid = false;
     m->dm = dm;
     m->tiles = tiles;
     m->list = list;
@@ -165,7 +179,7 @@ void cva_model_destroy(cva_model* m)
 
 int cva_set_precision(cva_model* m, int mode)
 {
-    if (!m || (mode != CVA_PRECISION_EXACT && mode != CVA_PRECISION_SPLIT_BF16)) return CVA_ERR_INVALID_ARG;
+    if (!m || (mode != CVA_PRECISION_MIXED && mode != CVA_PRECISION_FP64)) return CVA_ERR_INVALID_ARG;
     m->precision = mode;
     return CVA_OK;
 }
@@ -189,6 +203,9 @@ int cva_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, in
         cva::launch_fit_moments(cube, B, P, labels, K, m->dm, m->xtr, m->tiles, m->list, m->cap, m->num_sms, s);
     if (e == cudaSuccess) e = cva::launch_fit_finalize(m->dm, B, K, m->nvec, s);
     if (e == cudaSuccess) e = cva::launch_train_range(B, K, m->xtr, m->dm, m->nvec, m->num_sms, s);
+    m->fit_nvec = m->nvec;
+    m->range64_valid = false;
+    if (e == cudaSuccess && m->precision == CVA_PRECISION_FP64) e = ensure_range64(m, s);
     return from_cuda(e);
 }
 
@@ -211,9 +228,22 @@ int cva_model_get(cva_model* m, double* eigvals, double* V, double* mean, float*
         return CVA_ERR_CUDA;
     if (mean && cudaMemcpy(mean, dm->mu, sizeof(double) * B, cudaMemcpyDeviceToHost) != cudaSuccess)
         return CVA_ERR_CUDA;
-    if (train_range &&
-        cudaMemcpy(train_range, dm->train_range, sizeof(float) * 2 * B, cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (train_range && m->precision == CVA_PRECISION_FP64) {
+        unsigned long long enc[2 * cva::MAXB];
+        if (ensure_range64(m, static_cast<cudaStream_t>(stream)) != cudaSuccess ||
+            cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess ||
+            cudaMemcpy(enc, dm->train_enc64, sizeof(enc), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return CVA_ERR_CUDA;
+        for (int i = 0; i < 2 * B; ++i) {
+            const unsigned long long b = cva::ord_dec_bits(enc[i]);
+            double d;
+            std::memcpy(&d, &b, sizeof(d));
+            train_range[i] = i < 2 * m->fit_nvec ? static_cast<float>(d) : 0.0f;
+        }
+    } else if (train_range &&
+               cudaMemcpy(train_range, dm->train_range, sizeof(float) * 2 * B, cudaMemcpyDeviceToHost) != cudaSuccess) {
         return CVA_ERR_CUDA;
+    }
     if (V && cudaMemcpy2D(V, sizeof(double) * B, dm->V, sizeof(double) * cva::MAXB, sizeof(double) * B, B,
                           cudaMemcpyDeviceToHost) != cudaSuccess)
         return CVA_ERR_CUDA;
@@ -250,7 +280,7 @@ int cva_model_get_scatter(cva_model* m, int64_t* counts, double* class_means, do
 int cva_project(const uint16_t* cube, int B, int H, int W, cva_model* m, int k, float* out_f32,
                 float* range_out, void* stream)
 {
-    if (!m || B != m->B || !valid_dims(B, H, W) || k < 1 || k > m->nvec) return CVA_ERR_INVALID_ARG;
+    if (!m || B != m->B || !valid_dims(B, H, W) || k < 1 || k > m->fit_nvec) return CVA_ERR_INVALID_ARG;
     if (!out_f32 && !range_out) return CVA_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(cube) % 2 != 0 || reinterpret_cast<uintptr_t>(out_f32) % 4 != 0 ||
         reinterpret_cast<uintptr_t>(range_out) % 4 != 0)
@@ -260,6 +290,14 @@ int cva_project(const uint16_t* cube, int B, int H, int W, cva_model* m, int k, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long P = static_cast<long long>(H) * W;
     cudaError_t e = cudaSuccess;
+    if (m->precision == CVA_PRECISION_FP64) {
+        unsigned long long* acc = range_out ? m->dm->work_enc64 : nullptr;
+        if (acc) e = cva::launch_enc_init(acc, k, s);
+        if (e == cudaSuccess)
+            e = cva::launch_project64(cube, B, P, m->dm, k, out_f32, nullptr, nullptr, nullptr, acc, m->num_sms, s);
+        if (e == cudaSuccess && acc) e = cva::launch_enc_to_float(acc, k, range_out, s);
+        return from_cuda(e);
+    }
     if (range_out) e = cva::launch_range_init(range_out, k, s);
     if (e == cudaSuccess)
         e = cva::launch_project(cube, B, P, m->dm, k, out_f32, nullptr, nullptr, range_out, m->num_sms, s);
@@ -285,7 +323,7 @@ int cva_to_u8(const float* proj, int k, int H, int W, int mode, const float* ran
             if (e == cudaSuccess) e = cva::launch_f32_to_u8(proj, k, P, dmc, m->dm->work_range, out, m->num_sms, s);
             break;
         case CVA_RANGE_TRAINING:
-            if (!m || k > m->nvec) return CVA_ERR_INVALID_ARG;
+            if (!m || k > m->fit_nvec) return CVA_ERR_INVALID_ARG;
             e = cva::launch_f32_to_u8(proj, k, P, dmc, m->dm->train_range, out, m->num_sms, s);
             break;
         case CVA_RANGE_GIVEN: {
@@ -308,13 +346,40 @@ int cva_to_u8(const float* proj, int k, int H, int W, int mode, const float* ran
 int cva_project_u8(const uint16_t* cube, int B, int H, int W, cva_model* m, int k, int mode, const float* range,
                    uint8_t* out, void* stream)
 {
-    if (!m || B != m->B || !valid_dims(B, H, W) || k < 1 || k > m->nvec) return CVA_ERR_INVALID_ARG;
+    if (!m || B != m->B || !valid_dims(B, H, W) || k < 1 || k > m->fit_nvec) return CVA_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(cube) % 2 != 0) return CVA_ERR_INVALID_ARG;
     if (!device_visible(cube) || !device_visible(out)) return CVA_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long P = static_cast<long long>(H) * W;
     DevModel* dm = m->dm;
     cudaError_t e = cudaSuccess;
+    if (m->precision == CVA_PRECISION_FP64) {
+        switch (mode) {
+            case CVA_RANGE_TRAINING:
+                e = ensure_range64(m, s);
+                if (e == cudaSuccess)
+                    e = cva::launch_project64(cube, B, P, dm, k, nullptr, out, dm->train_enc64, nullptr, nullptr,
+                                              m->num_sms, s);
+                break;
+            case CVA_RANGE_GIVEN:
+                if (!range || !device_visible(range) || reinterpret_cast<uintptr_t>(range) % 4 != 0)
+                    return CVA_ERR_INVALID_ARG;
+                e = cva::launch_project64(cube, B, P, dm, k, nullptr, out, nullptr, range, nullptr, m->num_sms, s);
+                break;
+            case CVA_RANGE_GLOBAL:
+                e = cva::launch_enc_init(dm->work_enc64, k, s);
+                if (e == cudaSuccess)
+                    e = cva::launch_project64(cube, B, P, dm, k, nullptr, nullptr, nullptr, nullptr, dm->work_enc64,
+                                              m->num_sms, s);
+                if (e == cudaSuccess)
+                    e = cva::launch_project64(cube, B, P, dm, k, nullptr, out, dm->work_enc64, nullptr, nullptr,
+                                              m->num_sms, s);
+                break;
+            default:
+                return CVA_ERR_INVALID_ARG;
+        }
+        return from_cuda(e);
+    }
     switch (mode) {
         case CVA_RANGE_TRAINING:
             e = cva::launch_project(cube, B, P, dm, k, nullptr, out, dm->train_range, nullptr, m->num_sms, s);

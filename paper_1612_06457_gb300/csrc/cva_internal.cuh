@@ -88,6 +88,12 @@ struct DevModel {
     float dofs[MAXB];
     float train_range[2 * MAXB];  // (lo, hi) of each variate over the training pixels
     float work_range[2 * MAXB];   // scratch range for the two-pass global rescale
+
+    // ---- FP64 form (CVA_PRECISION_FP64) -------------------------------------
+    // (min, max) pairs of FP64 scores in the order-preserving 64-bit encoding
+    // of ord_enc, so that integer atomics give the extremes.
+    unsigned long long train_enc64[2 * MAXB];  // over the training pixels
+    unsigned long long work_enc64[2 * MAXB];   // scratch for range passes
 };
 
 // -------------------------------------------------------------------------
@@ -122,6 +128,18 @@ cudaError_t launch_f32_range(const float* proj, int k, long long P, const DevMod
 cudaError_t launch_f32_to_u8(const float* proj, int k, long long P, const DevModel* dm,
                              const float* range, uint8_t* out, int num_sms, cudaStream_t s);
 
+// FP64 form: the training range in FP64 (into dm->train_enc64), and the
+// projection with FP64 coefficients and accumulation.  The 8-bit range comes
+// from `u8_enc` (encoded FP64 pairs) when given, else from `u8_range`
+// (float pairs); `enc_acc` receives the encoded extremes when given.
+cudaError_t launch_train_range64(int B, int K, const uint16_t* xtr, DevModel* dm, int nvec, int num_sms,
+                                 cudaStream_t s);
+cudaError_t launch_enc_init(unsigned long long* enc, int k, cudaStream_t s);
+cudaError_t launch_enc_to_float(const unsigned long long* enc, int k, float* out, cudaStream_t s);
+cudaError_t launch_project64(const uint16_t* cube, int B, long long P, const DevModel* dm, int k,
+                             float* out_f32, uint8_t* out_u8, const unsigned long long* u8_enc,
+                             const float* u8_range, unsigned long long* enc_acc, int num_sms, cudaStream_t s);
+
 // -------------------------------------------------------------------------
 // device helpers
 // -------------------------------------------------------------------------
@@ -149,6 +167,17 @@ __device__ inline void atomic_max_float(float* addr, float v)
     if (!(v == v)) return;
     if (__float_as_int(v) >= 0) atomicMax(reinterpret_cast<int*>(addr), __float_as_int(v));
     else atomicMin(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
+}
+
+// Order-preserving map of a double onto a 64-bit unsigned integer (negative
+// values: all bits inverted; others: sign bit set), and its inverse.
+__host__ __device__ inline unsigned long long ord_enc_bits(unsigned long long b)
+{
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ inline unsigned long long ord_dec_bits(unsigned long long u)
+{
+    return (u >> 63) ? (u & 0x7FFFFFFFFFFFFFFFull) : ~u;
 }
 
 // The low (sel = 0) or high (sel = 1) 16-bit half of `w` as the float 2^23 + x:
