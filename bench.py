@@ -53,6 +53,7 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP64-form comparison")
+    ap.add_argument("--no-forms", action="store_true", help="batch workload: skip the per-page forms")
     return ap.parse_args()
 
 
@@ -458,9 +459,190 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+BATCH_WORKLOAD = "batch64_uneven"
+
+
+def _batch_config(ws):
+    P = sum(w.P for w in ws)
+    nb = sum(w.cube.nbytes + w.labels.nbytes for w in ws)
+    return {"workload": BATCH_WORKLOAD, "pages": len(ws), "pixels": P,
+            "bands": [min(w.B for w in ws), max(w.B for w in ws)],
+            "sides": [min(min(w.H, w.W) for w in ws), max(max(w.H, w.W) for w in ws)],
+            "classes": [min(w.K for w in ws), max(w.K for w in ws)],
+            "train_pixels": sum(sum(w.n_train) for w in ws), "variates": "K-1 per page",
+            "range": "training-score (second rescale)",
+            "l2": f"inputs larger than L2 ({nb / 1e6:.0f} MB > {L2_BYTES / 2**20:.0f} MiB)"}
+
+
+def _oracle_batch_time(ws, pages=2, rows=128):
+    """Oracle on a bounded sample of the batch: full fit of the first pages and
+    projection + rescale of `rows` rows of each, scaled to all pixels."""
+    t_fit = 0.0
+    t_px = 0.0
+    n_px = 0
+    fit_px = 0
+    for w in ws[:pages]:
+        tf, tr = _oracle_step_time(w, min(rows, w.H))
+        t_fit += tf
+        fit_px += w.P
+        t_px += tr
+        n_px += min(rows, w.H) * w.W
+    P = sum(w.P for w in ws)
+    est = t_fit * (P / fit_px) + t_px * (P / n_px)
+    return est, (f"oracle fit of the first {pages} pages ({fit_px} px) + projection/8-bit rescale of {rows} rows "
+                 f"of each, scaled to the batch's {P} pixels")
+
+
+def run_batch_bench(a):
+    import numpy as np
+    import torch
+
+    import paper_1612_06457_gb300 as cva
+    from synth import batch_workloads
+
+    world, rank, local = _dist_env()
+    if rank != 0:
+        return
+    ws = batch_workloads(64)
+    if a.impl == "reference":
+        ts = []
+        for i in range(a.warmup + a.steps):
+            t, sample = _oracle_batch_time(ws)
+            if i >= a.warmup:
+                ts.append(t)
+        t = statistics.median(ts)
+        v = sum(w.P for w in ws) / t / 1e6
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+                          "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": _batch_config(ws),
+                          "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                          "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+              flush=True)
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cva.load()
+    P = sum(w.P for w in ws)
+    host = [(torch.from_numpy(w.cube).pin_memory(), torch.from_numpy(w.labels).pin_memory()) for w in ws]
+    pages = [(c.to(dev), l.to(dev), w.K, w.k, torch.empty((w.k, w.H, w.W), dtype=torch.uint8, device=dev))
+             for (c, l), w in zip(host, ws)]
+    ntrain = sum(sum(w.n_train) for w in ws)
+    b = cva.Batch(len(ws), P, int(ntrain * 1.05) + 1024)
+    stream = torch.cuda.Stream(device=dev)
+    tuned = cva.cva_batch_tune(b, pages, stream=stream)
+    with torch.cuda.stream(stream):
+        cva.cva_fit_project_batched(b, pages, stream=stream)
+    torch.cuda.synchronize()
+    st = cva.cva_batch_status(b, len(ws), stream=stream)
+    if (st != cva.CVA_OK).any():
+        raise SystemExit(f"batch failed: {st.tolist()}")
+    g_step = torch.cuda.CUDAGraph()
+    g_proj = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_step, stream=stream):
+        cva.cva_fit_project_batched(b, pages, stream=stream)
+    with torch.cuda.graph(g_proj, stream=stream):
+        cva.cva_project_batched(b, pages, stream=stream)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    sampler.start()
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            g_step.replay()
+    ms = _time_graphs(torch, (g_step,), stream, a.steps)
+    clocks = sampler.stop()
+    proj_ms = _time_graphs(torch, (g_proj,), stream, a.steps)
+
+    # the same pages one after another through the single-page entry points
+    # (mixed form, then the FP64 form), each captured as one graph
+    forms = {}
+    form_list = () if a.no_forms else ((cva.CVA_PRECISION_MIXED, "per_page_mixed", max(3, a.steps // 4)),
+                                       (cva.CVA_PRECISION_FP64, "per_page_fp64", 3))
+    for mode, name, steps in form_list:
+        models = []
+        outs = []
+        for w, p in zip(ws, pages):
+            m = cva.Model(w.B, w.K)
+            cva.cva_set_variates(m, w.k)
+            cva.cva_set_precision(m, mode)
+            models.append(m)
+            outs.append(torch.empty_like(p[4]))
+        with torch.cuda.stream(stream):
+            for m, w, p, o in zip(models, ws, pages, outs):
+                cva.cva_fit(p[0], p[1], w.K, m, stream=stream)
+                cva.cva_project_u8(p[0], m, w.k, cva.CVA_RANGE_TRAINING, o, stream=stream)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for m, w, p, o in zip(models, ws, pages, outs):
+                cva.cva_fit(p[0], p[1], w.K, m, stream=stream)
+                cva.cva_project_u8(p[0], m, w.k, cva.CVA_RANGE_TRAINING, o, stream=stream)
+        t = _time_graphs(torch, (g,), stream, steps)
+        same = all(torch.equal(o, p[4]) for o, p in zip(outs, pages)) if mode == cva.CVA_PRECISION_MIXED else None
+        forms[name] = {"ms_per_step": t, "value": P / (t * 1e-3) / 1e6, "unit": UNIT, "steps": steps,
+                       "identical_images": same}
+        del g
+        for m in models:
+            m.close()
+
+    # end to end: pinned host -> device, batch, images -> host
+    outs_h = [torch.empty(p[4].shape, dtype=torch.uint8).pin_memory() for p in pages]
+    e2e_steps = max(2, min(a.steps, 5))
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            for (c_h, l_h), p in zip(host, pages):
+                p[0].copy_(c_h, non_blocking=True)
+                p[1].copy_(l_h, non_blocking=True)
+            cva.cva_fit_project_batched(b, pages, stream=stream)
+            for o_h, p in zip(outs_h, pages):
+                o_h.copy_(p[4], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+
+    peak, peak_kind = _peaks()
+    alg = sum(w.P * (2 * w.B + w.k) for w in ws)
+    achieved = alg / (proj_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": P / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": _batch_config(ws),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "kb_project_v8 (batched fused projection + u8)",
+                     "peak_kind": peak_kind, "alg_bytes_per_launch": alg, "launch_ms": proj_ms},
+        "e2e": {"value": P / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(w.cube.nbytes + w.labels.nbytes for w in ws)),
+                "d2h_bytes_per_step": int(sum(o.numel() for o in outs_h)), "ms_per_step": e2e_ms,
+                "steps": e2e_steps},
+        "gpu_launches": 11 * a.steps,
+        "clocks": clocks,
+        "autotuned": {"groups_per_item": tuned[0], "ctas_per_sm": tuned[1]},
+        "forms": forms,
+    }
+    for name in forms:
+        line["speedup_over_" + name] = forms[name]["ms_per_step"] / ms
+    if not a.no_cpu_baseline:
+        t, sample = _oracle_batch_time(ws)
+        line["cpu_baseline"] = {"value": P / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
 def main():
     a = _args()
-    if a.impl == "reference":
+    if a.workload == BATCH_WORKLOAD:
+        run_batch_bench(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

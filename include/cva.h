@@ -210,6 +210,68 @@ int cva_project_u8(const uint16_t* cube, int B, int H, int W, cva_model* m, int 
 int cva_fit_project_u8_noalloc(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, int K,
                                int k, uint8_t* out, double* eigvals, int* status, void* stream);
 
+/* ---- Batched form -------------------------------------------------------
+ * Many pages (cubes of uneven size, band count and class count) fitted and
+ * projected to 8 bits with the training-score range (CVA_RANGE_TRAINING), in
+ * one fixed sequence of about ten launches whatever the page count, so that a
+ * whole batch can be captured as one CUDA graph.  Each page is the problem of
+ * Section 2 on its own (its own classes, scatter matrices and eigenvectors);
+ * the results equal cva_fit + cva_project_u8 on each page. */
+#define CVA_MAX_BATCH_PAGES 4096
+#define CVA_MAX_BATCH_VARIATES 8
+
+typedef struct {
+    const uint16_t* cube;  /* device, B x H x W (2-byte aligned) */
+    const uint8_t* labels; /* device, H x W: 0 = unlabelled, c + 1 = class c */
+    uint8_t* out;          /* device, k x H x W */
+    double* eigvals;       /* device, B doubles, or NULL */
+    int B, H, W;           /* 1 <= B <= CVA_MAX_BANDS, H W < 2^31 */
+    int K;                 /* 2 <= K <= CVA_MAX_CLASSES */
+    int k;                 /* variates, 1 <= k <= min(B, CVA_MAX_BATCH_VARIATES) */
+} cva_page;
+
+typedef struct cva_batch cva_batch;
+
+/* Workspace for batches of up to max_pages pages holding up to max_pixels
+ * pixels in all and up to max_train training pixels in all (< 2^32).  Owns
+ * until cva_batch_destroy: one model block (~150 KB) per page, a tile
+ * workspace of 68 bytes per 16384 pixels, and pooled training storage of 84
+ * bytes per training pixel.  Allocates with cudaMalloc: call it outside stream
+ * capture.  *out is set to NULL on error. */
+int cva_batch_create(int max_pages, int64_t max_pixels, int64_t max_train, cva_batch** out);
+void cva_batch_destroy(cva_batch* b);
+
+/* Fit and project every page of `pages` (host array of n descriptors, read
+ * during the call only).  Asynchronous on `stream`; allocates nothing.
+ * Host checks (CVA_ERR_INVALID_ARG): n, every page's sizes, device-visible
+ * buffers; CVA_ERR_CAPACITY when the pages' pixels exceed the workspace.  A
+ * page whose labels exceed K, whose class is empty, whose S_w is not positive
+ * definite, or that overflows the pooled training storage fails alone: its
+ * output is left untouched and cva_batch_status reports it.  Calls on one
+ * workspace must not overlap on the GPU. */
+int cva_fit_project_batched(cva_batch* b, const cva_page* pages, int n, void* stream);
+
+/* The projection pass alone: project every page again with the models of
+ * the last cva_fit_project_batched on this workspace, which must have been
+ * given the same pages in the same order (same shapes and classes; the cube
+ * contents may differ, e.g. the same pages imaged again).  Asynchronous;
+ * allocates nothing. */
+int cva_project_batched(cva_batch* b, const cva_page* pages, int n, void* stream);
+
+/* Synchronize `stream` and copy each page's status of the last batch into
+ * status (host, n ints; CVA_OK, a device-side error, or CVA_ERR_NOT_FITTED).
+ * Returns CVA_OK or the first page's error. */
+int cva_batch_status(cva_batch* b, int n, int* status, void* stream);
+
+/* Autotuner of the batched projection: runs the batch once, then times the
+ * projection pass with each work-item size (1, 2, 4 or 8 groups of 2048
+ * pixels) and grid (two CTAs per SM, persistent; or one CTA per item) on
+ * `pages` and keeps the fastest for later calls on this workspace.
+ * Synchronizes `stream`; call it outside stream capture.  chosen (host, 2
+ * ints, or NULL) receives the groups per item and the CTAs per SM (0 = one
+ * per item). */
+int cva_batch_tune(cva_batch* b, const cva_page* pages, int n, void* stream, int* chosen);
+
 /* Human-readable text of a CVA_* code (static storage). */
 const char* cva_strerror(int code);
 

@@ -54,6 +54,12 @@ SIGNATURES = {
     "cva_to_u8": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "cva_project_u8": (_I, [_P, _I, _I, _I, _P, _I, _I, _P, _P, _P]),
     "cva_fit_project_u8_noalloc": (_I, [_P, _I, _I, _I, _P, _I, _I, _P, _P, _P, _P]),
+    "cva_batch_create": (_I, [_I, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p)]),
+    "cva_batch_destroy": (None, [_P]),
+    "cva_fit_project_batched": (_I, [_P, _P, _I, _P]),
+    "cva_batch_status": (_I, [_P, _I, _P, _P]),
+    "cva_project_batched": (_I, [_P, _P, _I, _P]),
+    "cva_batch_tune": (_I, [_P, _P, _I, _P, _P]),
     "cva_strerror": (ctypes.c_char_p, [_I]),
 }
 
@@ -243,3 +249,87 @@ def cva_fit_project_u8_noalloc(cube: torch.Tensor, labels: torch.Tensor, K: int,
                                            _dptr(eigvals, torch.float64, "eigvals"),
                                            _dptr(status, torch.int32, "status"), _stream_ptr(stream))
     _check(rc, "cva_fit_project_u8_noalloc")
+
+
+CVA_MAX_BATCH_PAGES = 4096
+CVA_MAX_BATCH_VARIATES = 8
+
+
+class cva_page(ctypes.Structure):
+    """One page of a batch (layout of ``cva_page`` in cva.h)."""
+    _fields_ = [("cube", ctypes.c_void_p), ("labels", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("eigvals", ctypes.c_void_p), ("B", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("K", ctypes.c_int), ("k", ctypes.c_int)]
+
+
+class Batch:
+    """Owner of one ``cva_batch`` workspace."""
+
+    def __init__(self, max_pages: int, max_pixels: int, max_train: int):
+        h = ctypes.c_void_p()
+        _check(load().cva_batch_create(max_pages, max_pixels, max_train, ctypes.byref(h)), "cva_batch_create")
+        self.handle = h
+        self.max_pages = max_pages
+
+    def close(self) -> None:
+        if self.handle:
+            load().cva_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cva_batch_create(max_pages: int, max_pixels: int, max_train: int) -> Batch:
+    return Batch(max_pages, max_pixels, max_train)
+
+
+def cva_batch_destroy(b: Batch) -> None:
+    b.close()
+
+
+def _pages(items):
+    """(cube, labels, K, k, out[, eigvals]) tuples -> ctypes array of cva_page."""
+    arr = (cva_page * len(items))()
+    for i, it in enumerate(items):
+        cube, labels, K, k, out = it[:5]
+        eig = it[5] if len(it) > 5 else None
+        B, H, W = cube.shape
+        if tuple(labels.shape) != (H, W) or tuple(out.shape) != (k, H, W):
+            raise ValueError(f"page {i}: labels must be H x W and out k x H x W")
+        arr[i] = cva_page(_dptr(cube, torch.uint16, "cube"), _dptr(labels, torch.uint8, "labels"),
+                          _dptr(out, torch.uint8, "out"), _dptr(eig, torch.float64, "eigvals"), B, H, W, K, k)
+    return arr
+
+
+def cva_fit_project_batched(b: Batch, pages, stream=None) -> None:
+    """Fit + fused 8-bit projection (training-score range) of every page.
+    ``pages``: sequence of (cube, labels, K, k, out[, eigvals]) device tensors."""
+    arr = _pages(pages)
+    _check(load().cva_fit_project_batched(b.handle, arr, len(pages), _stream_ptr(stream)), "cva_fit_project_batched")
+
+
+def cva_project_batched(b: Batch, pages, stream=None) -> None:
+    """The projection pass alone, with the models of the last batch on ``b``."""
+    arr = _pages(pages)
+    _check(load().cva_project_batched(b.handle, arr, len(pages), _stream_ptr(stream)), "cva_project_batched")
+
+
+def cva_batch_status(b: Batch, n: int, stream=None):
+    """Per-page status codes of the last batch (numpy int32 array)."""
+    import numpy as np
+
+    st = np.zeros(n, np.int32)
+    load().cva_batch_status(b.handle, n, ctypes.c_void_p(st.ctypes.data), _stream_ptr(stream))
+    return st
+
+
+def cva_batch_tune(b: Batch, pages, stream=None):
+    """Autotune the batched projection on ``pages``; returns (groups per item, CTAs per SM)."""
+    arr = _pages(pages)
+    chosen = (ctypes.c_int * 2)()
+    _check(load().cva_batch_tune(b.handle, arr, len(pages), _stream_ptr(stream), chosen), "cva_batch_tune")
+    return int(chosen[0]), int(chosen[1])

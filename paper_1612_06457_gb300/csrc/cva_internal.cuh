@@ -141,6 +141,70 @@ cudaError_t launch_project64(const uint16_t* cube, int B, long long P, const Dev
                              const float* u8_range, unsigned long long* enc_acc, int num_sms, cudaStream_t s);
 
 // -------------------------------------------------------------------------
+// batched form: many pages (cubes) in one set of launches
+// -------------------------------------------------------------------------
+
+// One page of a batch in device memory.  The first block is set from the
+// host's page list by the set-up kernel; the second by the pool scan once the
+// label counts are known.  Pages are kept in the caller's order, and the
+// flattened work of the batch (label tiles, training rows, moment units,
+// training-range items, projection items) is laid out page after page, so a
+// work index maps to its page by a binary search on the page's first index.
+struct PageDev {
+    const uint16_t* cube;   // B x H x W
+    const uint8_t* labels;  // H x W
+    uint8_t* out;           // k x H x W
+    double* eigvals;        // B doubles, or null
+    DevModel* dm;           // the page's model block
+    unsigned int* tiles;    // ntiles x (K + 1) words
+    long long P;            // H W
+    long long tile0;        // first label tile of the page
+    long long item0;        // first projection item of the page
+    int B, K, k, ntiles;
+    int vec;                // labels 16-byte aligned
+    int v8;                 // projected by the batched kernel (P % 8 == 0, aligned buffers)
+    // ---- set on the device ----
+    unsigned long long row0;    // first row of the page in the pooled training list
+    unsigned long long xoff;    // uint16 offset of its rows in the pooled training matrix
+    unsigned long long unit0;   // first moments unit (256 rows of one class)
+    unsigned long long titem0;  // first training-range item (256 rows)
+    unsigned long long nrows;   // training rows
+};
+
+// Totals of the device-side work of a batch (pool scan).
+struct BatchTotals {
+    unsigned long long rows, xtr, units, titems;
+};
+
+constexpr int BATCH_ROWS_PER_ITEM = 256;  // training rows per training-range item
+
+// Largest page index p with key(pages[p]) <= v (pages sorted by key).
+template <typename KeyFn>
+__host__ __device__ inline int find_page(const PageDev* pages, int n, unsigned long long v, KeyFn key)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (key(pages[mid]) <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+cudaError_t launch_batch_tile_count(const PageDev* pages, int n, long long ntiles_total, cudaStream_t s);
+cudaError_t launch_batch_tile_compact(const PageDev* pages, int n, long long ntiles_total, unsigned int* list_pool,
+                                      cudaStream_t s);
+cudaError_t launch_batch_gather(const PageDev* pages, int n, const BatchTotals* tot, const unsigned int* list_pool,
+                                uint16_t* xtr_pool, int num_sms, cudaStream_t s);
+cudaError_t launch_batch_moments(const PageDev* pages, int n, const BatchTotals* tot, const uint16_t* xtr_pool,
+                                 int max_b, int num_sms, cudaStream_t s);
+cudaError_t launch_batch_finalize(const PageDev* pages, int n, cudaStream_t s);
+cudaError_t launch_batch_train_range(const PageDev* pages, int n, const BatchTotals* tot,
+                                     const uint16_t* xtr_pool, int max_k, int num_sms, cudaStream_t s);
+cudaError_t launch_batch_project(const PageDev* pages, int n, long long items_total, int groups_per_item,
+                                 int grid, int max_k, cudaStream_t s);
+
+// -------------------------------------------------------------------------
 // device helpers
 // -------------------------------------------------------------------------
 

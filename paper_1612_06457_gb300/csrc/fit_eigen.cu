@@ -173,10 +173,8 @@ __device__ void complete_basis(FinSmem& sm, int B, int j0, int j1)
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm, int B, int K, int nvec)
+__device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restrict__ dm, int B, int K, int nvec)
 {
-    extern __shared__ __align__(16) unsigned char fin_dyn[];
-    FinSmem& sm = *reinterpret_cast<FinSmem*>(fin_dyn);
     const MomShape sh = mom_shape(B);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (dm->status != 0) return;  // an earlier pass already failed
@@ -602,6 +600,23 @@ __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm,
     }
 }
 
+__global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm, int B, int K, int nvec)
+{
+    extern __shared__ __align__(16) unsigned char fin_dyn[];
+    fit_finalize_body(*reinterpret_cast<FinSmem*>(fin_dyn), dm, B, K, nvec);
+}
+
+// Batched form: one CTA per page, all pages at once; the eigenvalues are
+// also copied to the page's output when it asks for them.
+__global__ void __launch_bounds__(TPB) kb_fit_finalize(const PageDev* __restrict__ pages)
+{
+    extern __shared__ __align__(16) unsigned char fin_dyn[];
+    const PageDev& pg = pages[blockIdx.x];
+    fit_finalize_body(*reinterpret_cast<FinSmem*>(fin_dyn), pg.dm, pg.B, pg.K, pg.k);
+    __syncthreads();
+    if (pg.eigvals && threadIdx.x < pg.B && pg.dm->status == 0) pg.eigvals[threadIdx.x] = pg.dm->lam[threadIdx.x];
+}
+
 // Sb = Mb Mb^T for the statistics getter (not on the fit path).
 __global__ void k_scatter_sb(DevModel* __restrict__ dm, int B, int K)
 {
@@ -621,6 +636,15 @@ cudaError_t launch_fit_finalize(DevModel* dm, int B, int K, int nvec, cudaStream
     cudaError_t e = cudaFuncSetAttribute(k_fit_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_fit_finalize<<<1, TPB, smem, s>>>(dm, B, K, nvec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finalize(const PageDev* pages, int n, cudaStream_t s)
+{
+    const int smem = static_cast<int>(sizeof(FinSmem));
+    cudaError_t e = cudaFuncSetAttribute(kb_fit_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kb_fit_finalize<<<static_cast<unsigned>(n), TPB, smem, s>>>(pages);
     return cudaGetLastError();
 }
 

@@ -210,9 +210,11 @@ __device__ void scan_tiles(int ntiles, int K, int B, long long cap, int any_bad,
     }
 }
 
-__global__ void __launch_bounds__(TPB)
-k_tile_count(const uint8_t* __restrict__ labels, long long P, int K, int B, int vec, long long cap, int ntiles,
-             unsigned int* __restrict__ tiles, DevModel* __restrict__ dm)
+// One tile's class counts (tile `tile` of the page); the page's last CTA to
+// finish takes the prefix sums.
+__device__ __forceinline__ void tile_count_body(const uint8_t* __restrict__ labels, long long P, int K, int B, int vec,
+                                                long long cap, int ntiles, unsigned int* __restrict__ tiles,
+                                                DevModel* __restrict__ dm, int tile)
 {
     __shared__ unsigned long long wsum[NW][4];
     __shared__ int bad;
@@ -220,7 +222,7 @@ k_tile_count(const uint8_t* __restrict__ labels, long long P, int K, int B, int 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) bad = 0;
     uint32_t w[4][4];
-    load_tile(labels, static_cast<long long>(blockIdx.x) * TILE, P, vec, w);
+    load_tile(labels, static_cast<long long>(tile) * TILE, P, vec, w);
     unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
     const uint32_t kpat = static_cast<uint32_t>(K) * 0x01010101u;
     uint32_t over = 0;
@@ -253,7 +255,7 @@ k_tile_count(const uint8_t* __restrict__ labels, long long P, int K, int B, int 
                 for (int w2 = 0; w2 < NW; ++w2) t[q] += wsum[w2][q];
             v = field(t, tid);
         }
-        tiles[static_cast<long long>(blockIdx.x) * (K + 1) + tid] = v;
+        tiles[static_cast<long long>(tile) * (K + 1) + tid] = v;
     }
     // the last CTA to finish (atomic ticket after a fence) scans the counts;
     // no CTA ever waits for another
@@ -270,18 +272,23 @@ k_tile_count(const uint8_t* __restrict__ labels, long long P, int K, int B, int 
 }
 
 __global__ void __launch_bounds__(TPB)
-k_tile_compact(const uint8_t* __restrict__ labels, long long P, int K, int vec,
-               const unsigned int* __restrict__ tiles, unsigned int* __restrict__ list,
-               const DevModel* __restrict__ dm)
+k_tile_count(const uint8_t* __restrict__ labels, long long P, int K, int B, int vec, long long cap, int ntiles,
+             unsigned int* __restrict__ tiles, DevModel* __restrict__ dm)
+{
+    tile_count_body(labels, P, K, B, vec, cap, ntiles, tiles, dm, blockIdx.x);
+}
+
+__device__ __forceinline__ void tile_compact_body(const uint8_t* __restrict__ labels, long long P, int K, int vec,
+                                                  const unsigned int* __restrict__ tiles,
+                                                  unsigned int* __restrict__ list, int tile)
 {
     __shared__ unsigned long long wsum[NW][4];
     __shared__ unsigned int base[MAXK];
     const int tid = threadIdx.x;
-    if (dm->status != 0) return;
-    const long long t0 = static_cast<long long>(blockIdx.x) * TILE;
+    const long long t0 = static_cast<long long>(tile) * TILE;
     uint32_t w[4][4];
     load_tile(labels, t0, P, vec, w);
-    if (tid < K) base[tid] = tiles[static_cast<long long>(blockIdx.x) * (K + 1) + tid];
+    if (tid < K) base[tid] = tiles[static_cast<long long>(tile) * (K + 1) + tid];
     const uint32_t kpat = static_cast<uint32_t>(K) * 0x01010101u;
     // training-label masks (nonzero and <= K) and per-class counts of the 64 labels
     uint32_t mask[4];
@@ -313,8 +320,44 @@ k_tile_compact(const uint8_t* __restrict__ labels, long long P, int K, int vec,
     }
 }
 
-// One thread per listed training pixel, all its band loads in flight: the
-// augmented row (x_0 .. x_{B-1}, 1, 0 ..) of the class-major training matrix.
+__global__ void __launch_bounds__(TPB)
+k_tile_compact(const uint8_t* __restrict__ labels, long long P, int K, int vec,
+               const unsigned int* __restrict__ tiles, unsigned int* __restrict__ list,
+               const DevModel* __restrict__ dm)
+{
+    if (dm->status != 0) return;
+    tile_compact_body(labels, P, K, vec, tiles, list, blockIdx.x);
+}
+
+// The augmented row (x_0 .. x_{B-1}, 1, 0 ..) of listed training pixel i,
+// all its band loads in flight, stored as one 16-byte-aligned row.
+__device__ __forceinline__ void gather_row(const uint16_t* __restrict__ cube, int B, long long P,
+                                           const unsigned int* __restrict__ list, uint16_t* __restrict__ xtr,
+                                           unsigned int i)
+{
+    const int BR = xtr_row(B);
+    const uint16_t* src = cube + list[i];
+    uint32_t xv[MAXB];
+    #pragma unroll
+    for (int b = 0; b < MAXB; ++b) xv[b] = (b < B) ? static_cast<uint32_t>(__ldg(src + static_cast<long long>(b) * P)) : 0u;
+    uint4* grow = reinterpret_cast<uint4*>(xtr + static_cast<long long>(i) * BR);
+    #pragma unroll
+    for (int q = 0; q < (MAXB + 8) / 8; ++q) {
+        if (q * 8 < BR) {
+            uint32_t pk[4];
+            #pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int b0 = q * 8 + 2 * h, b1 = b0 + 1;
+                const uint32_t v0 = (b0 < B) ? xv[b0 < MAXB ? b0 : 0] : (b0 == B ? 1u : 0u);
+                const uint32_t v1 = (b1 < B) ? xv[b1 < MAXB ? b1 : 0] : (b1 == B ? 1u : 0u);
+                pk[h] = v0 | (v1 << 16);
+            }
+            grow[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+    }
+}
+
+// One thread per listed training pixel: the class-major training matrix.
 __global__ void __launch_bounds__(TPB)
 k_gather(const uint16_t* __restrict__ cube, int B, long long P, int K, const unsigned int* __restrict__ list,
          uint16_t* __restrict__ xtr, const DevModel* __restrict__ dm)
@@ -322,29 +365,8 @@ k_gather(const uint16_t* __restrict__ cube, int B, long long P, int K, const uns
     if (dm->status != 0) return;
     unsigned int N = 0;
     for (int c = 0; c < K; ++c) N += dm->cls_count[c];
-    const int BR = xtr_row(B);
     const unsigned int stride = gridDim.x * TPB;
-    for (unsigned int i = blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
-        const uint16_t* src = cube + list[i];
-        uint32_t xv[MAXB];
-        #pragma unroll
-        for (int b = 0; b < MAXB; ++b) xv[b] = (b < B) ? static_cast<uint32_t>(__ldg(src + static_cast<long long>(b) * P)) : 0u;
-        uint4* grow = reinterpret_cast<uint4*>(xtr + static_cast<long long>(i) * BR);
-        #pragma unroll
-        for (int q = 0; q < (MAXB + 8) / 8; ++q) {
-            if (q * 8 < BR) {
-                uint32_t pk[4];
-                #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int b0 = q * 8 + 2 * h, b1 = b0 + 1;
-                    const uint32_t v0 = (b0 < B) ? xv[b0 < MAXB ? b0 : 0] : (b0 == B ? 1u : 0u);
-                    const uint32_t v1 = (b1 < B) ? xv[b1 < MAXB ? b1 : 0] : (b1 == B ? 1u : 0u);
-                    pk[h] = v0 | (v1 << 16);
-                }
-                grow[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            }
-        }
-    }
+    for (unsigned int i = blockIdx.x * TPB + threadIdx.x; i < N; i += stride) gather_row(cube, B, P, list, xtr, i);
 }
 
 // ldmatrix / mma.sync wrappers (bf16 inputs, f32 accumulators)
@@ -379,6 +401,101 @@ __device__ inline uint32_t bf16_of_byte(uint32_t v)
 constexpr int UPAD = UNIT + 8;  // shared row stride (bf16) of the transposed unit: conflict-free ldmatrix
 constexpr int MAXPAIR = MAXBA * (MAXBA + 1) / 2;
 
+// (a, b) of every upper-triangle entry a <= b of the (B+1) x (B+1) augmented
+// moment matrix, in row-major order.
+__device__ __forceinline__ void build_pairs(unsigned char* pa, unsigned char* pb, int BA)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int a = warp; a < BA; a += NW)
+        for (int b = a + lane; b < BA; b += 32) {
+            const int q = a * BA - a * (a - 1) / 2 + (b - a);
+            pa[q] = static_cast<unsigned char>(a);
+            pb[q] = static_cast<unsigned char>(b);
+        }
+}
+
+// Merge a thread's (up to three) moment sums into class c of the model.
+__device__ __forceinline__ void moments_flush(DevModel* __restrict__ dm, int c, int nb, int npair,
+                                              const unsigned char* pa, const unsigned char* pb,
+                                              unsigned long long (&acc)[3])
+{
+    #pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int q = threadIdx.x + k * TPB;
+        if (q < npair && acc[k]) {
+            const int a = pa[q], b = pb[q];
+            atomicAdd(&dm->mom[c][blk_index(a >> 2, b >> 2, nb)][(a & 3) * 4 + (b & 3)], acc[k]);
+        }
+        acc[k] = 0ull;
+    }
+}
+
+// One unit: rows [row0, row0 + len) of the training matrix (row length F)
+// split into bytes, transposed into shared memory, its Gram matrix formed on
+// the tensor cores and added to the thread's moment sums.  Every thread of
+// the CTA takes part (three barriers).
+__device__ __forceinline__ void moments_unit(uint16_t* XT, float* Cs, const uint16_t* __restrict__ xtr, int F,
+                                             unsigned int row0, int len, int npair, const unsigned char* pa,
+                                             const unsigned char* pb, unsigned long long (&acc)[3])
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int F2 = 2 * F;
+    const int MT = F2 / 16, NTL = F2 / 8;
+    // split and transpose: thread tid owns pixel column tid of the unit
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(xtr + static_cast<long long>(row0 + tid) * F);
+        #pragma unroll
+        for (int q = 0; q < (MAXB + 8) / 8; ++q) {
+            if (q * 8 < F) {
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (tid < len) v = __ldg(src + q);
+                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+                #pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                    const uint32_t x = (wv[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
+                    const int f = q * 8 + h;
+                    XT[f * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x >> 8));
+                    XT[(F + f) * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x & 0xFFu));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // Gram matrix of the split unit, one 16 x 8 output tile per warp at a time
+    for (int t = warp; t < MT * NTL; t += NW) {
+        const int mt = t / NTL, nt = t - (t / NTL) * NTL;
+        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const uint16_t* arow = XT + (mt * 16 + (lane & 15)) * UPAD + ((lane >> 4) << 3);
+        const uint16_t* brow = XT + (nt * 8 + (lane & 7)) * UPAD + (((lane >> 3) & 1) << 3);
+        #pragma unroll 4
+        for (int ks = 0; ks < UNIT / 16; ++ks) {
+            uint32_t af[4], bfr[2];
+            ldsm_x4(af, arow + ks * 16);
+            ldsm_x2(bfr, brow + ks * 16);
+            mma_bf16_16816(d, af, bfr);
+        }
+        const int r0 = mt * 16 + (lane >> 2), c0 = nt * 8 + (lane & 3) * 2;
+        Cs[r0 * F2 + c0] = d[0];
+        Cs[r0 * F2 + c0 + 1] = d[1];
+        Cs[(r0 + 8) * F2 + c0] = d[2];
+        Cs[(r0 + 8) * F2 + c0 + 1] = d[3];
+    }
+    __syncthreads();
+    #pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int q = tid + k * TPB;
+        if (q < npair) {
+            const int a = pa[q], b = pb[q];
+            const unsigned long long hh = __float2uint_rn(Cs[a * F2 + b]);
+            const unsigned long long hl = __float2uint_rn(Cs[a * F2 + F + b]);
+            const unsigned long long lh = __float2uint_rn(Cs[(F + a) * F2 + b]);
+            const unsigned long long ll = __float2uint_rn(Cs[(F + a) * F2 + F + b]);
+            acc[k] += (hh << 16) + ((hl + lh) << 8) + ll;
+        }
+    }
+    __syncthreads();
+}
+
 // Exact moments on the tensor cores.  A unit holds up to 256 training rows of
 // one class.  Every 16-bit value x is split into its high and low bytes,
 // x = 256 h + l, both exact in bf16; the unit is stored transposed in shared
@@ -402,7 +519,7 @@ k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevMode
     const int BA = B + 1;
     const int npair = BA * (BA + 1) / 2;
     const int nb = mom_shape(B).nb;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     uint16_t* XT = reinterpret_cast<uint16_t*>(dyn);                     // F2 x UPAD bf16
     float* Cs = reinterpret_cast<float*>(dyn + F2 * UPAD * 2);           // F2 x F2
 
@@ -421,96 +538,132 @@ k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevMode
         ustart[K] = units;
         stop = (dm->status != 0) || (tot > static_cast<unsigned long long>(cap));
     }
-    for (int a = warp; a < BA; a += NW)
-        for (int b = a + lane; b < BA; b += 32) {
-            const int q = a * BA - a * (a - 1) / 2 + (b - a);
-            pa[q] = static_cast<unsigned char>(a);
-            pb[q] = static_cast<unsigned char>(b);
-        }
+    build_pairs(pa, pb, BA);
     __syncthreads();
     if (stop) return;
 
     unsigned long long acc[3] = {0ull, 0ull, 0ull};
     int cur_class = -1;
-    const int MT = F2 / 16, NTL = F2 / 8;
-
-    auto flush = [&](int c) {
-        #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int q = tid + k * TPB;
-            if (q < npair && acc[k]) {
-                const int a = pa[q], b = pb[q];
-                atomicAdd(&dm->mom[c][blk_index(a >> 2, b >> 2, nb)][(a & 3) * 4 + (b & 3)], acc[k]);
-            }
-            acc[k] = 0ull;
-        }
-    };
-
     const unsigned int nunits = ustart[K];
     for (unsigned int u = blockIdx.x; u < nunits; u += gridDim.x) {
         int c = 0;
         while (u >= ustart[c + 1]) ++c;
         if (c != cur_class) {
-            if (cur_class >= 0) flush(cur_class);
+            if (cur_class >= 0) moments_flush(dm, cur_class, nb, npair, pa, pb, acc);
             cur_class = c;
         }
         const unsigned int row0 = cstart[c] + (u - ustart[c]) * UNIT;
         const int len = static_cast<int>(min(static_cast<unsigned int>(UNIT), cstart[c] + ccount[c] - row0));
-        // split and transpose: thread tid owns pixel column tid of the unit
-        {
-            const uint4* src = reinterpret_cast<const uint4*>(xtr + static_cast<long long>(row0 + tid) * F);
-            #pragma unroll
-            for (int q = 0; q < (MAXB + 8) / 8; ++q) {
-                if (q * 8 < F) {
-                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                    if (tid < len) v = __ldg(src + q);
-                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-                    #pragma unroll
-                    for (int h = 0; h < 8; ++h) {
-                        const uint32_t x = (wv[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
-                        const int f = q * 8 + h;
-                        XT[f * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x >> 8));
-                        XT[(F + f) * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x & 0xFFu));
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // Gram matrix of the split unit, one 16 x 8 output tile per warp at a time
-        for (int t = warp; t < MT * NTL; t += NW) {
-            const int mt = t / NTL, nt = t - (t / NTL) * NTL;
-            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            const uint16_t* arow = XT + (mt * 16 + (lane & 15)) * UPAD + ((lane >> 4) << 3);
-            const uint16_t* brow = XT + (nt * 8 + (lane & 7)) * UPAD + (((lane >> 3) & 1) << 3);
-            #pragma unroll 4
-            for (int ks = 0; ks < UNIT / 16; ++ks) {
-                uint32_t af[4], bfr[2];
-                ldsm_x4(af, arow + ks * 16);
-                ldsm_x2(bfr, brow + ks * 16);
-                mma_bf16_16816(d, af, bfr);
-            }
-            const int r0 = mt * 16 + (lane >> 2), c0 = nt * 8 + (lane & 3) * 2;
-            Cs[r0 * F2 + c0] = d[0];
-            Cs[r0 * F2 + c0 + 1] = d[1];
-            Cs[(r0 + 8) * F2 + c0] = d[2];
-            Cs[(r0 + 8) * F2 + c0 + 1] = d[3];
-        }
-        __syncthreads();
-        #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int q = tid + k * TPB;
-            if (q < npair) {
-                const int a = pa[q], b = pb[q];
-                const unsigned long long hh = __float2uint_rn(Cs[a * F2 + b]);
-                const unsigned long long hl = __float2uint_rn(Cs[a * F2 + F + b]);
-                const unsigned long long lh = __float2uint_rn(Cs[(F + a) * F2 + b]);
-                const unsigned long long ll = __float2uint_rn(Cs[(F + a) * F2 + F + b]);
-                acc[k] += (hh << 16) + ((hl + lh) << 8) + ll;
-            }
-        }
-        __syncthreads();
+        moments_unit(XT, Cs, xtr, F, row0, len, npair, pa, pb, acc);
     }
-    if (cur_class >= 0) flush(cur_class);
+    if (cur_class >= 0) moments_flush(dm, cur_class, nb, npair, pa, pb, acc);
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: the same passes over the flattened work of many pages.
+// ---------------------------------------------------------------------------
+
+__device__ inline int page_of_tile(const PageDev* pages, int n, unsigned long long t)
+{
+    return find_page(pages, n, t, [](const PageDev& q) { return static_cast<unsigned long long>(q.tile0); });
+}
+
+__global__ void __launch_bounds__(TPB) kb_tile_count(const PageDev* __restrict__ pages, int n)
+{
+    const int p = page_of_tile(pages, n, blockIdx.x);
+    const PageDev& pg = pages[p];
+    // the training capacity is checked by the pool scan, over the whole batch
+    tile_count_body(pg.labels, pg.P, pg.K, pg.B, pg.vec, 0x7FFFFFFFFFFFFFFFll, pg.ntiles, pg.tiles, pg.dm,
+                    static_cast<int>(blockIdx.x - pg.tile0));
+}
+
+__global__ void __launch_bounds__(TPB)
+kb_tile_compact(const PageDev* __restrict__ pages, int n, unsigned int* __restrict__ list_pool)
+{
+    const int p = page_of_tile(pages, n, blockIdx.x);
+    const PageDev& pg = pages[p];
+    if (pg.dm->status != 0) return;
+    tile_compact_body(pg.labels, pg.P, pg.K, pg.vec, pg.tiles, list_pool + pg.row0,
+                      static_cast<int>(blockIdx.x - pg.tile0));
+}
+
+// One thread per pooled training row; rows of failed pages are skipped.
+__global__ void __launch_bounds__(TPB)
+kb_gather(const PageDev* __restrict__ pages, int n, const BatchTotals* __restrict__ tot,
+          const unsigned int* __restrict__ list_pool, uint16_t* __restrict__ xtr_pool)
+{
+    const unsigned long long rows = tot->rows;
+    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * TPB;
+    for (unsigned long long r = static_cast<unsigned long long>(blockIdx.x) * TPB + threadIdx.x; r < rows; r += stride) {
+        const int p = find_page(pages, n, r, [](const PageDev& q) { return q.row0; });
+        const PageDev& pg = pages[p];
+        if (pg.dm->status != 0) continue;
+        gather_row(pg.cube, pg.B, pg.P, list_pool + pg.row0, xtr_pool + pg.xoff,
+                   static_cast<unsigned int>(r - pg.row0));
+    }
+}
+
+// Moment units of all pages: a unit is up to 256 rows of one class of one
+// page.  A CTA keeps its sums in registers while it stays on one (page,
+// class) and merges them into that page's model when it moves on.
+__global__ void __launch_bounds__(TPB)
+kb_moments(const PageDev* __restrict__ pages, int n, const BatchTotals* __restrict__ tot,
+           const uint16_t* __restrict__ xtr_pool, int max_f)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ unsigned char pa[MAXPAIR], pb[MAXPAIR];
+    __shared__ int s_page, s_class, s_len, s_skip;
+    __shared__ unsigned int s_row0;
+    const int tid = threadIdx.x;
+    uint16_t* XT = reinterpret_cast<uint16_t*>(dyn);                          // (2 max_f) x UPAD bf16
+    float* Cs = reinterpret_cast<float*>(dyn + 2 * max_f * UPAD * 2);         // (2 max_f)^2
+
+    unsigned long long acc[3] = {0ull, 0ull, 0ull};
+    int cur_page = -1, cur_class = -1, cur_b = -1;
+    const unsigned long long nunits = tot->units;
+    for (unsigned long long u = blockIdx.x; u < nunits; u += gridDim.x) {
+        if (tid == 0) {
+            const int p = find_page(pages, n, u, [](const PageDev& q) { return q.unit0; });
+            const PageDev& pg = pages[p];
+            unsigned long long lu = u - pg.unit0;
+            unsigned int row = 0;
+            int c = 0;
+            for (; c < pg.K; ++c) {
+                const unsigned int nc = pg.dm->cls_count[c];
+                const unsigned long long nu = (nc + UNIT - 1) / UNIT;
+                if (lu < nu) break;
+                lu -= nu;
+                row += nc;
+            }
+            const unsigned int row0 = row + static_cast<unsigned int>(lu) * UNIT;
+            s_page = p;
+            s_class = c;
+            s_row0 = row0;
+            s_len = static_cast<int>(min(static_cast<unsigned int>(UNIT), row + pg.dm->cls_count[c < pg.K ? c : 0] - row0));
+            s_skip = pg.dm->status != 0 || c >= pg.K;
+        }
+        __syncthreads();
+        const int p = s_page, c = s_class;
+        const PageDev& pg = pages[p];
+        const int B = pg.B, BA = B + 1;
+        const int npair = BA * (BA + 1) / 2;
+        if (p != cur_page || c != cur_class) {
+            if (cur_page >= 0) moments_flush(pages[cur_page].dm, cur_class, mom_shape(cur_b).nb, (cur_b + 1) * (cur_b + 2) / 2,
+                                             pa, pb, acc);
+            if (B != cur_b) {
+                __syncthreads();  // flush read the old tables
+                build_pairs(pa, pb, BA);
+                __syncthreads();
+            }
+            cur_page = p;
+            cur_class = c;
+            cur_b = B;
+        }
+        if (!s_skip) moments_unit(XT, Cs, xtr_pool + pg.xoff, xtr_row(B), s_row0, s_len, npair, pa, pb, acc);
+        else __syncthreads();
+    }
+    if (cur_page >= 0)
+        moments_flush(pages[cur_page].dm, cur_class, mom_shape(cur_b).nb, (cur_b + 1) * (cur_b + 2) / 2, pa, pb, acc);
 }
 
 }  // namespace
@@ -540,6 +693,41 @@ cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const u
     // useful maximum and let idle CTAs exit at once
     const long long g3 = static_cast<long long>(num_sms) * 4;
     k_moments<<<static_cast<unsigned>(g3), TPB, smem, s>>>(B, K, xtr, cap, dm);
+    return cudaGetLastError();
+}
+
+}  // namespace cva
+
+namespace cva {
+
+cudaError_t launch_batch_tile_count(const PageDev* pages, int n, long long ntiles_total, cudaStream_t s)
+{
+    kb_tile_count<<<static_cast<unsigned>(ntiles_total), TPB, 0, s>>>(pages, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_tile_compact(const PageDev* pages, int n, long long ntiles_total, unsigned int* list_pool,
+                                      cudaStream_t s)
+{
+    kb_tile_compact<<<static_cast<unsigned>(ntiles_total), TPB, 0, s>>>(pages, n, list_pool);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_gather(const PageDev* pages, int n, const BatchTotals* tot, const unsigned int* list_pool,
+                                uint16_t* xtr_pool, int num_sms, cudaStream_t s)
+{
+    kb_gather<<<static_cast<unsigned>(num_sms * 8), TPB, 0, s>>>(pages, n, tot, list_pool, xtr_pool);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_moments(const PageDev* pages, int n, const BatchTotals* tot, const uint16_t* xtr_pool,
+                                 int max_b, int num_sms, cudaStream_t s)
+{
+    const int F = xtr_row(max_b);
+    const size_t smem = static_cast<size_t>(2 * F) * UPAD * 2 + static_cast<size_t>(2 * F) * (2 * F) * 4;
+    cudaError_t e = cudaFuncSetAttribute(kb_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kb_moments<<<static_cast<unsigned>(num_sms * 4), TPB, smem, s>>>(pages, n, tot, xtr_pool, F);
     return cudaGetLastError();
 }
 

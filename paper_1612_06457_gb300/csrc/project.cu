@@ -140,6 +140,78 @@ __device__ inline void accumulate8(float (&acc)[KV][8], const uint4& w, const fl
     }
 }
 
+// Pixels 8 g .. 8 g + 7 of one cube (plane = P / 8 groups per band): the
+// pipelined band loads, the FP32 projection onto KV variates, and the stores.
+// GUARD drops the outputs of variates kc .. KV-1 (batched pages with fewer
+// variates than the launch).
+template <int KV, bool F32, bool U8, bool RNG, bool GUARD>
+__device__ __forceinline__ void project_group8(const uint16_t* __restrict__ cube, int B, long long P, long long g,
+                                               const ProjSmem<KV>& sm, int j0, int kc, float* __restrict__ out_f32,
+                                               uint8_t* __restrict__ out_u8, float (&mn)[KV], float (&mx)[KV])
+{
+    const long long plane = P / 8;  // band stride in uint4 units
+    const uint4* src = reinterpret_cast<const uint4*>(cube) + g;
+    float acc[KV][8];
+    #pragma unroll
+    for (int j = 0; j < KV; ++j)
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) acc[j][i] = 0.0f;
+    uint4 wa[8], wb[8];
+    #pragma unroll
+    for (int u = 0; u < 8; ++u)
+        if (u < B) wa[u] = __ldcs(src + u * plane);
+    for (int b0 = 0;; b0 += 16) {
+        // the batch tests are the same for every thread: whole batches are
+        // skipped by branches, only a partial last batch is predicated
+        const bool second = b0 + 8 < B;
+        if (second) {
+            #pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (b0 + 8 + u < B) wb[u] = __ldcs(src + (b0 + 8 + u) * plane);
+        }
+        #pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (b0 + u < B) accumulate8<KV>(acc, wa[u], sm.V[b0 + u], sm.shift[b0 + u]);
+        if (!second) break;
+        const bool third = b0 + 16 < B;
+        if (third) {
+            #pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (b0 + 16 + u < B) wa[u] = __ldcs(src + (b0 + 16 + u) * plane);
+        }
+        #pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (b0 + 8 + u < B) accumulate8<KV>(acc, wb[u], sm.V[b0 + 8 + u], sm.shift[b0 + 8 + u]);
+        if (!third) break;
+    }
+    const long long p = g * 8;
+    #pragma unroll
+    for (int j = 0; j < KV; ++j) {
+        if (GUARD && j >= kc) break;
+        float y[8];
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) y[i] = __fsub_rn(acc[j][i], sm.d[j]);
+        if (F32) {
+            float4* dst = reinterpret_cast<float4*>(out_f32 + static_cast<long long>(j0 + j) * P + p);
+            __stcs(dst, make_float4(y[0], y[1], y[2], y[3]));
+            __stcs(dst + 1, make_float4(y[4], y[5], y[6], y[7]));
+        }
+        if (U8) {
+            const float sc = sm.scale[j], of = sm.off[j];
+            uint32_t c[8];
+            #pragma unroll
+            for (int i = 0; i < 8; ++i) c[i] = to_code(y[i], sc, of);
+            const uint2 packed = make_uint2(c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24),
+                                            c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24));
+            __stcs(reinterpret_cast<uint2*>(out_u8 + static_cast<long long>(j0 + j) * P + p), packed);
+        }
+        if (RNG) {
+            #pragma unroll
+            for (int i = 0; i < 8; ++i) { mn[j] = fminf(mn[j], y[i]); mx[j] = fmaxf(mx[j], y[i]); }
+        }
+    }
+}
+
 template <int KV, bool F32, bool U8, bool RNG>
 __global__ void __launch_bounds__(TPB, 2)
 k_project_v8(const uint16_t* __restrict__ cube, int B, long long P, const DevModel* __restrict__ dm,
@@ -156,69 +228,9 @@ k_project_v8(const uint16_t* __restrict__ cube, int B, long long P, const DevMod
     for (int j = 0; j < KV; ++j) { mn[j] = __int_as_float(0x7F800000); mx[j] = __int_as_float(0xFF800000); }
 
     const long long ngroups = P / 8;
-    const long long plane = P / 8;  // band stride in uint4 units
     const long long stride = static_cast<long long>(gridDim.x) * TPB;
-    for (long long g = static_cast<long long>(blockIdx.x) * TPB + threadIdx.x; g < ngroups; g += stride) {
-        const uint4* src = reinterpret_cast<const uint4*>(cube) + g;
-        float acc[KV][8];
-        #pragma unroll
-        for (int j = 0; j < KV; ++j)
-            #pragma unroll
-            for (int i = 0; i < 8; ++i) acc[j][i] = 0.0f;
-        uint4 wa[8], wb[8];
-        #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (u < B) wa[u] = __ldcs(src + u * plane);
-        for (int b0 = 0;; b0 += 16) {
-            // the batch tests are the same for every thread: whole batches are
-            // skipped by branches, only a partial last batch is predicated
-            const bool second = b0 + 8 < B;
-            if (second) {
-                #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (b0 + 8 + u < B) wb[u] = __ldcs(src + (b0 + 8 + u) * plane);
-            }
-            #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (b0 + u < B) accumulate8<KV>(acc, wa[u], sm.V[b0 + u], sm.shift[b0 + u]);
-            if (!second) break;
-            const bool third = b0 + 16 < B;
-            if (third) {
-                #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (b0 + 16 + u < B) wa[u] = __ldcs(src + (b0 + 16 + u) * plane);
-            }
-            #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (b0 + 8 + u < B) accumulate8<KV>(acc, wb[u], sm.V[b0 + 8 + u], sm.shift[b0 + 8 + u]);
-            if (!third) break;
-        }
-        const long long p = g * 8;
-        #pragma unroll
-        for (int j = 0; j < KV; ++j) {
-            float y[8];
-            #pragma unroll
-            for (int i = 0; i < 8; ++i) y[i] = __fsub_rn(acc[j][i], sm.d[j]);
-            if (F32) {
-                float4* dst = reinterpret_cast<float4*>(out_f32 + static_cast<long long>(j0 + j) * P + p);
-                __stcs(dst, make_float4(y[0], y[1], y[2], y[3]));
-                __stcs(dst + 1, make_float4(y[4], y[5], y[6], y[7]));
-            }
-            if (U8) {
-                const float sc = sm.scale[j], of = sm.off[j];
-                uint32_t c[8];
-                #pragma unroll
-                for (int i = 0; i < 8; ++i) c[i] = to_code(y[i], sc, of);
-                const uint2 packed = make_uint2(c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24),
-                                                c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24));
-                __stcs(reinterpret_cast<uint2*>(out_u8 + static_cast<long long>(j0 + j) * P + p), packed);
-            }
-            if (RNG) {
-                #pragma unroll
-                for (int i = 0; i < 8; ++i) { mn[j] = fminf(mn[j], y[i]); mx[j] = fmaxf(mx[j], y[i]); }
-            }
-        }
-    }
+    for (long long g = static_cast<long long>(blockIdx.x) * TPB + threadIdx.x; g < ngroups; g += stride)
+        project_group8<KV, F32, U8, RNG, false>(cube, B, P, g, sm, j0, KV, out_f32, out_u8, mn, mx);
     if (RNG) reduce_range<KV>(sm, mn, mx, KV, range_acc, j0);
 }
 
@@ -262,6 +274,41 @@ k_project_s(const uint16_t* __restrict__ cube, int B, long long P, long long p_b
 // Training-score range of variates [j0, j0 + kc): same FP32 operations as the
 // projection, on the rows of the gathered training matrix (x_0 .. x_{B-1}, 1, 0 ..).
 template <int KV>
+__device__ __forceinline__ void train_row(const ProjSmem<KV>& sm, const uint16_t* __restrict__ xrow, int B, int BR,
+                                          float (&mn)[KV], float (&mx)[KV])
+{
+    const uint4* row = reinterpret_cast<const uint4*>(xrow);
+    uint32_t pk[(MAXB + 8) / 2];
+    #pragma unroll
+    for (int q = 0; q < (MAXB + 8) / 8; ++q) {
+        if (q * 8 < BR) {
+            const uint4 v = __ldg(row + q);
+            pk[4 * q] = v.x; pk[4 * q + 1] = v.y; pk[4 * q + 2] = v.z; pk[4 * q + 3] = v.w;
+        } else {
+            pk[4 * q] = pk[4 * q + 1] = pk[4 * q + 2] = pk[4 * q + 3] = 0u;
+        }
+    }
+    float acc[KV];
+    #pragma unroll
+    for (int j = 0; j < KV; ++j) acc[j] = 0.0f;
+    #pragma unroll
+    for (int b = 0; b < MAXB; ++b) {
+        if (b < B) {
+            const uint32_t w = pk[b >> 1];
+            const float xs = __fsub_rn((b & 1) ? u16_hi_biased(w) : u16_lo_biased(w), sm.shift[b]);
+            #pragma unroll
+            for (int j = 0; j < KV; ++j) acc[j] = __fmaf_rn(sm.V[b][j], xs, acc[j]);
+        }
+    }
+    #pragma unroll
+    for (int j = 0; j < KV; ++j) {
+        const float y = __fsub_rn(acc[j], sm.d[j]);
+        mn[j] = fminf(mn[j], y);
+        mx[j] = fmaxf(mx[j], y);
+    }
+}
+
+template <int KV>
 __global__ void __launch_bounds__(TPB)
 k_train_range(int B, int K, const uint16_t* __restrict__ xtr, DevModel* __restrict__ dm, int j0)
 {
@@ -276,38 +323,74 @@ k_train_range(int B, int K, const uint16_t* __restrict__ xtr, DevModel* __restri
     #pragma unroll
     for (int j = 0; j < KV; ++j) { mn[j] = __int_as_float(0x7F800000); mx[j] = __int_as_float(0xFF800000); }
     const unsigned int stride = gridDim.x * TPB;
-    for (unsigned int i = blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
-        const uint4* row = reinterpret_cast<const uint4*>(xtr + static_cast<long long>(i) * BR);
-        uint32_t pk[(MAXB + 8) / 2];
-        #pragma unroll
-        for (int q = 0; q < (MAXB + 8) / 8; ++q) {
-            if (q * 8 < BR) {
-                const uint4 v = __ldg(row + q);
-                pk[4 * q] = v.x; pk[4 * q + 1] = v.y; pk[4 * q + 2] = v.z; pk[4 * q + 3] = v.w;
-            } else {
-                pk[4 * q] = pk[4 * q + 1] = pk[4 * q + 2] = pk[4 * q + 3] = 0u;
-            }
+    for (unsigned int i = blockIdx.x * TPB + threadIdx.x; i < N; i += stride)
+        train_row<KV>(sm, xtr + static_cast<long long>(i) * BR, B, BR, mn, mx);
+    reduce_range<KV>(sm, mn, mx, KV, dm->train_range, j0);
+}
+
+// ---------------------------------------------------------------------------
+// Batched form.  Training-range items are 256 rows of one page; projection
+// items are `gpi` groups of TPB x 8 pixels of one page.  A CTA walks its
+// items in order and reloads the coefficients (and, for the range, merges
+// its extremes) when the page changes; pages that failed are skipped.
+// ---------------------------------------------------------------------------
+template <int KV>
+__global__ void __launch_bounds__(TPB)
+kb_train_range(const PageDev* __restrict__ pages, int n, const BatchTotals* __restrict__ tot,
+               const uint16_t* __restrict__ xtr_pool)
+{
+    __shared__ ProjSmem<KV> sm;
+    float mn[KV], mx[KV];
+    int cur = -1;
+    const unsigned long long nitems = tot->titems;
+    for (unsigned long long it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int p = find_page(pages, n, it, [](const PageDev& q) { return q.titem0; });
+        const PageDev& pg = pages[p];
+        if (pg.dm->status != 0 || !pg.dm->fitted) continue;
+        if (p != cur) {
+            if (cur >= 0) reduce_range<KV>(sm, mn, mx, pages[cur].k, pages[cur].dm->train_range, 0);
+            __syncthreads();
+            load_coefs<KV>(sm, pg.dm, pg.B, 0, pg.k, nullptr, false);
+            __syncthreads();
+            #pragma unroll
+            for (int j = 0; j < KV; ++j) { mn[j] = __int_as_float(0x7F800000); mx[j] = __int_as_float(0xFF800000); }
+            cur = p;
         }
-        float acc[KV];
-        #pragma unroll
-        for (int j = 0; j < KV; ++j) acc[j] = 0.0f;
-        #pragma unroll
-        for (int b = 0; b < MAXB; ++b) {
-            if (b < B) {
-                const uint32_t w = pk[b >> 1];
-                const float xs = __fsub_rn((b & 1) ? u16_hi_biased(w) : u16_lo_biased(w), sm.shift[b]);
-                #pragma unroll
-                for (int j = 0; j < KV; ++j) acc[j] = __fmaf_rn(sm.V[b][j], xs, acc[j]);
-            }
+        const unsigned long long i = (it - pg.titem0) * BATCH_ROWS_PER_ITEM + threadIdx.x;
+        const int BR = xtr_row(pg.B);
+        if (threadIdx.x < BATCH_ROWS_PER_ITEM && i < pg.nrows)
+            train_row<KV>(sm, xtr_pool + pg.xoff + i * BR, pg.B, BR, mn, mx);
+    }
+    if (cur >= 0) reduce_range<KV>(sm, mn, mx, pages[cur].k, pages[cur].dm->train_range, 0);
+}
+
+template <int KV>
+__global__ void __launch_bounds__(TPB, 2)
+kb_project_v8(const PageDev* __restrict__ pages, int n, long long nitems, int gpi)
+{
+    __shared__ ProjSmem<KV> sm;
+    float mn[KV], mx[KV];
+    int cur = -1;
+    for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int p = find_page(pages, n, static_cast<unsigned long long>(it),
+                                [](const PageDev& q) { return static_cast<unsigned long long>(q.item0); });
+        const PageDev& pg = pages[p];
+        if (pg.dm->status != 0 || !pg.dm->fitted) continue;
+        if (p != cur) {
+            __syncthreads();
+            load_coefs<KV>(sm, pg.dm, pg.B, 0, pg.k, pg.dm->train_range, true);
+            __syncthreads();
+            cur = p;
         }
-        #pragma unroll
-        for (int j = 0; j < KV; ++j) {
-            const float y = __fsub_rn(acc[j], sm.d[j]);
-            mn[j] = fminf(mn[j], y);
-            mx[j] = fmaxf(mx[j], y);
+        const long long ngroups = pg.P / 8;
+        const long long g0 = (it - pg.item0) * static_cast<long long>(gpi) * TPB + threadIdx.x;
+        for (int r = 0; r < gpi; ++r) {
+            const long long g = g0 + static_cast<long long>(r) * TPB;
+            if (g < ngroups)
+                project_group8<KV, false, true, false, true>(pg.cube, pg.B, pg.P, g, sm, 0, pg.k, nullptr, pg.out,
+                                                             mn, mx);
         }
     }
-    reduce_range<KV>(sm, mn, mx, KV, dm->train_range, j0);
 }
 
 __global__ void k_range_init(float* range, int k)
@@ -468,13 +551,51 @@ cudaError_t launch_train_range(int B, int K, const uint16_t* xtr, DevModel* dm, 
     return cudaSuccess;
 }
 
+cudaError_t launch_batch_train_range(const PageDev* pages, int n, const BatchTotals* tot,
+                                     const uint16_t* xtr_pool, int max_k, int num_sms, cudaStream_t s)
+{
+    const int grid = num_sms * 4;
+    switch (max_k) {
+        case 1: kb_train_range<1><<<grid, TPB, 0, s>>>(pages, n, tot, xtr_pool); break;
+        case 2: kb_train_range<2><<<grid, TPB, 0, s>>>(pages, n, tot, xtr_pool); break;
+        case 3: kb_train_range<3><<<grid, TPB, 0, s>>>(pages, n, tot, xtr_pool); break;
+        case 4: kb_train_range<4><<<grid, TPB, 0, s>>>(pages, n, tot, xtr_pool); break;
+        case 5: kb_train_range<5><<<grid, TPB, 0, s>>>(pages, n, tot, xtr_pool); break;
+        case 6: kb_train_range<6><<<grid, TPB, 0, s>>>(pages, n, tot, xtr_pool); break;
+        case 7: kb_train_range<7><<<grid, TPB, 0, s>>>(pages, n, tot, xtr_pool); break;
+        case 8: kb_train_range<8><<<grid, TPB, 0, s>>>(pages, n, tot, xtr_pool); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_project(const PageDev* pages, int n, long long items_total, int groups_per_item,
+                                 int grid, int max_k, cudaStream_t s)
+{
+    if (items_total < 1) return cudaSuccess;
+    const long long g = grid < items_total ? grid : items_total;
+    const unsigned gx = static_cast<unsigned>(g);
+    switch (max_k) {
+        case 1: kb_project_v8<1><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
+        case 2: kb_project_v8<2><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
+        case 3: kb_project_v8<3><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
+        case 4: kb_project_v8<4><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
+        case 5: kb_project_v8<5><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
+        case 6: kb_project_v8<6><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
+        case 7: kb_project_v8<7><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
+        case 8: kb_project_v8<8><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_project(const uint16_t* cube, int B, long long P, const DevModel* dm, int k,
                            float* out_f32, uint8_t* out_u8, const float* u8_range, float* range_acc,
                            int num_sms, cudaStream_t s)
 {
     const bool aligned = (P % 8 == 0) && (reinterpret_cast<uintptr_t>(cube) % 16 == 0) &&
                          (!out_f32 || reinterpret_cast<uintptr_t>(out_f32) % 16 == 0) &&
-                         (!out_u8 || reinterpret_cast<uintptr_t>(out_u8) % 4 == 0);
+                         (!out_u8 || reinterpret_cast<uintptr_t>(out_u8) % 8 == 0);
     const bool f32 = out_f32 != nullptr, u8 = out_u8 != nullptr, rng = range_acc != nullptr;
     for (int j0 = 0; j0 < k; j0 += KCH) {
         const int kc = (k - j0) < KCH ? (k - j0) : KCH;
