@@ -54,6 +54,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP64-form comparison")
     ap.add_argument("--no-forms", action="store_true", help="batch workload: skip the per-page forms")
+    ap.add_argument("--pages", type=int, default=64, help="batch workload: number of pages (64 = the benchmark)")
     return ap.parse_args()
 
 
@@ -503,7 +504,7 @@ def run_batch_bench(a):
     world, rank, local = _dist_env()
     if rank != 0:
         return
-    ws = batch_workloads(64)
+    ws = batch_workloads(a.pages)
     if a.impl == "reference":
         ts = []
         for i in range(a.warmup + a.steps):

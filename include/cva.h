@@ -265,7 +265,8 @@ int cva_batch_status(cva_batch* b, int n, int* status, void* stream);
 
 /* Autotuner of the batched projection: runs the batch once, then times the
  * projection pass with each work-item size (1, 2, 4 or 8 groups of 2048
- * pixels) and grid (two CTAs per SM, persistent; or one CTA per item) on
+ * pixels) and grid (two persistent CTAs per SM, each on a contiguous run of
+ * items; or one CTA per item) on
  * `pages` and keeps the fastest for later calls on this workspace.
  * Synchronizes `stream`; call it outside stream capture.  chosen (host, 2
  * ints, or NULL) receives the groups per item and the CTAs per SM (0 = one

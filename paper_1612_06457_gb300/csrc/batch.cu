@@ -74,6 +74,20 @@ __global__ void kb_setup(SetupChunk c, PageDev* __restrict__ pages)
     d.v8 = h.v8;
 }
 
+// Page of every label tile and every projection item (one CTA per page).
+__global__ void kb_fill_pages(const PageDev* __restrict__ pages, int gpi, int* __restrict__ tile_page,
+                              int* __restrict__ item_page)
+{
+    const int p = blockIdx.x;
+    const PageDev& pg = pages[p];
+    for (int t = threadIdx.x; t < pg.ntiles; t += blockDim.x) tile_page[pg.tile0 + t] = p;
+    if (pg.v8) {
+        const long long per = static_cast<long long>(gpi) * ITEM_TPB;
+        const long long items = (pg.P / 8 + per - 1) / per;
+        for (long long i = threadIdx.x; i < items; i += blockDim.x) item_page[pg.item0 + i] = p;
+    }
+}
+
 struct Quad {
     unsigned long long v[4];
 };
@@ -159,11 +173,11 @@ kb_pool_scan(PageDev* __restrict__ pages, int n, BatchTotals* __restrict__ tot, 
     }
 }
 
-__global__ void kb_status(const PageDev* __restrict__ pages, int n, int* __restrict__ status)
+__global__ void kb_status(const DevModel* __restrict__ dms, int n, int* __restrict__ status)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < n) {
-        const DevModel* dm = pages[p].dm;
+        const DevModel* dm = dms + p;
         const int st = dm->status;
         status[p] = (st == 0 && !dm->fitted) ? CVA_ERR_NOT_FITTED : st;
     }
@@ -196,8 +210,11 @@ struct cva_batch {
     uint16_t* xtr;
     BatchTotals* tot;
     int* status;
+    int* tile_page;        // page of every label tile
+    int* item_page;        // page of every projection item
+    long long max_items;   // entries of item_page
     int gpi;               // pixel groups (TPB x 8 pixels) per projection item
-    int grid_per_sm;       // projection CTAs per SM (0: one CTA per item)
+    int grid_per_sm;       // persistent projection CTAs per SM, each on a contiguous run of items (0: one CTA per item)
     PageDev* host_pages;   // scratch for building the table
 };
 
@@ -212,63 +229,79 @@ void free_batch(cva_batch* b)
     cudaFree(b->xtr);
     cudaFree(b->tot);
     cudaFree(b->status);
+    cudaFree(b->tile_page);
+    cudaFree(b->item_page);
     delete[] b->host_pages;
     delete b;
 }
 
 // Host-side page table and the batch's sizes; returns CVA_OK or an error.
+// The table holds the pages sorted by their variate count k (stable), so that
+// the projection items of each k form one range, projected by one launch of
+// the kernel compiled for that k; page i keeps model block i.
 struct Plan {
     long long tiles_total;
     long long items_total;
+    long long kbeg[MAX_BATCH_VARIATES + 1], kend[MAX_BATCH_VARIATES + 1];  // items of each k
     int max_b, max_k;
 };
 
 int plan_batch(cva_batch* b, const cva_page* pages, int n, Plan* plan)
 {
     if (!b || !pages || n < 1 || n > b->max_pages) return CVA_ERR_INVALID_ARG;
-    long long tile0 = 0, item0 = 0, words = 0;
-    int max_b = 1, max_k = 1;
     for (int i = 0; i < n; ++i) {
         const cva_page& q = pages[i];
         if (q.B < 1 || q.B > CVA_MAX_BANDS || q.K < 2 || q.K > CVA_MAX_CLASSES || q.H < 1 || q.W < 1 ||
             q.k < 1 || q.k > q.B || q.k > MAX_BATCH_VARIATES)
             return CVA_ERR_INVALID_ARG;
-        const long long P = static_cast<long long>(q.H) * q.W;
-        if (P >= (1LL << 31)) return CVA_ERR_INVALID_ARG;
+        if (static_cast<long long>(q.H) * q.W >= (1LL << 31)) return CVA_ERR_INVALID_ARG;
         if (reinterpret_cast<uintptr_t>(q.cube) % 2 != 0) return CVA_ERR_INVALID_ARG;
         if (!device_visible(q.cube) || !device_visible(q.labels) || !device_visible(q.out) ||
             (q.eigvals && !device_visible(q.eigvals)))
             return CVA_ERR_INVALID_ARG;
-        const long long ntiles = (P + cva::LABEL_TILE - 1) / cva::LABEL_TILE;
-        PageDev& d = b->host_pages[i];
-        std::memset(&d, 0, sizeof(d));
-        d.cube = q.cube;
-        d.labels = q.labels;
-        d.out = q.out;
-        d.eigvals = q.eigvals;
-        d.dm = b->dms + i;
-        d.tiles = b->tiles + words;
-        d.P = P;
-        d.tile0 = tile0;
-        d.B = q.B;
-        d.K = q.K;
-        d.k = q.k;
-        d.ntiles = static_cast<int>(ntiles);
-        d.vec = (reinterpret_cast<uintptr_t>(q.labels) % 16 == 0) ? 1 : 0;
-        d.v8 = (P % 8 == 0) && (reinterpret_cast<uintptr_t>(q.cube) % 16 == 0) &&
-               (reinterpret_cast<uintptr_t>(q.out) % 8 == 0);
-        d.item0 = item0;
-        if (d.v8) {
-            const long long groups = P / 8;
-            const long long per = static_cast<long long>(b->gpi) * ITEM_TPB;
-            item0 += (groups + per - 1) / per;
-        }
-        words += ntiles * (q.K + 1);
-        tile0 += ntiles;
-        if (q.B > max_b) max_b = q.B;
-        if (q.k > max_k) max_k = q.k;
     }
-    if (words > b->tiles_cap) return CVA_ERR_CAPACITY;
+    long long tile0 = 0, item0 = 0, words = 0;
+    int max_b = 1, max_k = 1;
+    int t = 0;  // table position
+    plan->kbeg[0] = plan->kend[0] = 0;
+    for (int kk = 1; kk <= MAX_BATCH_VARIATES; ++kk) {
+        plan->kbeg[kk] = item0;
+        for (int i = 0; i < n; ++i) {
+            const cva_page& q = pages[i];
+            if (q.k != kk) continue;
+            const long long P = static_cast<long long>(q.H) * q.W;
+            const long long ntiles = (P + cva::LABEL_TILE - 1) / cva::LABEL_TILE;
+            PageDev& d = b->host_pages[t++];
+            std::memset(&d, 0, sizeof(d));
+            d.cube = q.cube;
+            d.labels = q.labels;
+            d.out = q.out;
+            d.eigvals = q.eigvals;
+            d.dm = b->dms + i;
+            d.tiles = b->tiles + words;
+            d.P = P;
+            d.tile0 = tile0;
+            d.B = q.B;
+            d.K = q.K;
+            d.k = q.k;
+            d.ntiles = static_cast<int>(ntiles);
+            d.vec = (reinterpret_cast<uintptr_t>(q.labels) % 16 == 0) ? 1 : 0;
+            d.v8 = (P % 8 == 0) && (reinterpret_cast<uintptr_t>(q.cube) % 16 == 0) &&
+                   (reinterpret_cast<uintptr_t>(q.out) % 8 == 0);
+            d.item0 = item0;
+            if (d.v8) {
+                const long long groups = P / 8;
+                const long long per = static_cast<long long>(b->gpi) * ITEM_TPB;
+                item0 += (groups + per - 1) / per;
+            }
+            words += ntiles * (q.K + 1);
+            tile0 += ntiles;
+            if (q.B > max_b) max_b = q.B;
+            if (q.k > max_k) max_k = q.k;
+        }
+        plan->kend[kk] = item0;
+    }
+    if (words > b->tiles_cap || tile0 > b->tiles_cap || item0 > b->max_items) return CVA_ERR_CAPACITY;
     if (tile0 >= (1LL << 31)) return CVA_ERR_INVALID_ARG;
     plan->tiles_total = tile0;
     plan->items_total = item0;
@@ -289,7 +322,8 @@ cudaError_t upload_pages(cva_batch* b, int n, cudaStream_t s)
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    kb_fill_pages<<<n, 256, 0, s>>>(b->pages, b->gpi, b->tile_page, b->item_page);
+    return cudaGetLastError();
 }
 
 int projection_grid(const cva_batch* b, long long items)
@@ -300,8 +334,13 @@ int projection_grid(const cva_batch* b, long long items)
 
 cudaError_t launch_projection(cva_batch* b, int n, const Plan& plan, cudaStream_t s)
 {
-    cudaError_t e = cva::launch_batch_project(b->pages, n, plan.items_total, b->gpi,
-                                              projection_grid(b, plan.items_total), plan.max_k, s);
+    cudaError_t e = cudaSuccess;
+    for (int k = 1; k <= MAX_BATCH_VARIATES && e == cudaSuccess; ++k) {
+        const long long items = plan.kend[k] - plan.kbeg[k];
+        if (items > 0)
+            e = cva::launch_batch_project(b->pages, b->item_page, plan.kbeg[k], plan.kend[k], b->gpi,
+                                          projection_grid(b, items), k, s);
+    }
     // pages the batched kernel does not take (pixel count or alignment)
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         const PageDev& d = b->host_pages[i];
@@ -315,13 +354,13 @@ cudaError_t launch_projection(cva_batch* b, int n, const Plan& plan, cudaStream_
 cudaError_t run_batch(cva_batch* b, int n, const Plan& plan, cudaStream_t s)
 {
     cudaError_t e = upload_pages(b, n, s);
-    if (e == cudaSuccess) e = cva::launch_batch_tile_count(b->pages, n, plan.tiles_total, s);
+    if (e == cudaSuccess) e = cva::launch_batch_tile_count(b->pages, b->tile_page, plan.tiles_total, s);
     if (e == cudaSuccess) {
         kb_pool_scan<<<1, 1024, 0, s>>>(b->pages, n, b->tot, static_cast<unsigned long long>(b->max_train),
                                         static_cast<unsigned long long>(b->max_train) * XTR_POOL_ROW);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cva::launch_batch_tile_compact(b->pages, n, plan.tiles_total, b->list, s);
+    if (e == cudaSuccess) e = cva::launch_batch_tile_compact(b->pages, b->tile_page, plan.tiles_total, b->list, s);
     if (e == cudaSuccess) e = cva::launch_batch_gather(b->pages, n, b->tot, b->list, b->xtr, b->num_sms, s);
     if (e == cudaSuccess) e = cva::launch_batch_moments(b->pages, n, b->tot, b->xtr, plan.max_b, b->num_sms, s);
     if (e == cudaSuccess) e = cva::launch_batch_finalize(b->pages, n, s);
@@ -353,6 +392,7 @@ int cva_batch_create(int max_pages, int64_t max_pixels, int64_t max_train, cva_b
     b->num_sms = sms;
     b->max_pages = max_pages;
     b->tiles_cap = (max_pixels / cva::LABEL_TILE + max_pages) * static_cast<long long>(CVA_MAX_CLASSES + 1);
+    b->max_items = max_pixels / (8 * ITEM_TPB) + max_pages;
     b->max_train = max_train;
     b->gpi = 2;
     b->grid_per_sm = 2;
@@ -365,6 +405,8 @@ int cva_batch_create(int max_pages, int64_t max_pixels, int64_t max_train, cva_b
     ok = ok && cudaMalloc(&b->xtr, sizeof(uint16_t) * max_train * XTR_POOL_ROW) == cudaSuccess;
     ok = ok && cudaMalloc(&b->tot, sizeof(BatchTotals)) == cudaSuccess;
     ok = ok && cudaMalloc(&b->status, sizeof(int) * max_pages) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->tile_page, sizeof(int) * b->tiles_cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->item_page, sizeof(int) * b->max_items) == cudaSuccess;
     ok = ok && cudaMemset(b->dms, 0, sizeof(DevModel) * max_pages) == cudaSuccess;
     ok = ok && cudaMemset(b->pages, 0, sizeof(PageDev) * max_pages) == cudaSuccess;
     if (!ok) {
@@ -406,7 +448,7 @@ int cva_batch_status(cva_batch* b, int n, int* status, void* stream)
 {
     if (!b || !status || n < 1 || n > b->max_pages) return CVA_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    kb_status<<<(n + 255) / 256, 256, 0, s>>>(b->pages, n, b->status);
+    kb_status<<<(n + 255) / 256, 256, 0, s>>>(b->dms, n, b->status);
     if (cudaGetLastError() != cudaSuccess) return CVA_ERR_CUDA;
     if (cudaMemcpyAsync(status, b->status, sizeof(int) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
@@ -429,13 +471,13 @@ int cva_batch_tune(cva_batch* b, const cva_page* pages, int n, void* stream, int
         cudaEventDestroy(e0);
         return CVA_ERR_CUDA;
     }
-    static const int kGpi[] = {1, 2, 4, 8};
+    static const int kGpi[] = {2, 4, 8, 16, 32};
     static const int kGrid[] = {2, 0};
     float best = 0.0f;
     int best_gpi = b->gpi, best_grid = b->grid_per_sm;
     bool fail = false;
     for (int gi = 0; gi < 2 && !fail; ++gi)
-        for (int pi = 0; pi < 4 && !fail; ++pi) {
+        for (int pi = 0; pi < 5 && !fail; ++pi) {
             b->gpi = kGpi[pi];
             b->grid_per_sm = kGrid[gi];
             if (plan_batch(b, pages, n, &plan) != CVA_OK || upload_pages(b, n, s) != cudaSuccess) {

@@ -191,9 +191,11 @@ __host__ __device__ inline int find_page(const PageDev* pages, int n, unsigned l
     return lo;
 }
 
-cudaError_t launch_batch_tile_count(const PageDev* pages, int n, long long ntiles_total, cudaStream_t s);
-cudaError_t launch_batch_tile_compact(const PageDev* pages, int n, long long ntiles_total, unsigned int* list_pool,
-                                      cudaStream_t s);
+// `tile_page` / `item_page`: page of every label tile / projection item.
+cudaError_t launch_batch_tile_count(const PageDev* pages, const int* tile_page, long long ntiles_total,
+                                    cudaStream_t s);
+cudaError_t launch_batch_tile_compact(const PageDev* pages, const int* tile_page, long long ntiles_total,
+                                      unsigned int* list_pool, cudaStream_t s);
 cudaError_t launch_batch_gather(const PageDev* pages, int n, const BatchTotals* tot, const unsigned int* list_pool,
                                 uint16_t* xtr_pool, int num_sms, cudaStream_t s);
 cudaError_t launch_batch_moments(const PageDev* pages, int n, const BatchTotals* tot, const uint16_t* xtr_pool,
@@ -201,8 +203,8 @@ cudaError_t launch_batch_moments(const PageDev* pages, int n, const BatchTotals*
 cudaError_t launch_batch_finalize(const PageDev* pages, int n, cudaStream_t s);
 cudaError_t launch_batch_train_range(const PageDev* pages, int n, const BatchTotals* tot,
                                      const uint16_t* xtr_pool, int max_k, int num_sms, cudaStream_t s);
-cudaError_t launch_batch_project(const PageDev* pages, int n, long long items_total, int groups_per_item,
-                                 int grid, int max_k, cudaStream_t s);
+cudaError_t launch_batch_project(const PageDev* pages, const int* item_page, long long it_begin, long long it_end,
+                                 int groups_per_item, int grid, int k, cudaStream_t s);
 
 // -------------------------------------------------------------------------
 // device helpers

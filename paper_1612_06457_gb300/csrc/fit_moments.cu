@@ -15,13 +15,15 @@
 //   k_tile_count    training pixels of each class in the tile, and whether
 //                   the tile holds a label above K; the last CTA to finish
 //                   (atomic ticket, no waiting) then takes the prefix sums of
-//                   the tile counts class by class, giving each tile its
-//                   first row in every class segment of the class-major
-//                   training list, and writes the class totals, the fit's
-//                   status word and the reset of the moment accumulators;
+//                   the tile counts (one warp per class), giving each tile
+//                   its first row within every class segment of the
+//                   class-major training list, and writes the class totals,
+//                   the fit's status word and the reset of the moment
+//                   accumulators;
 //   k_tile_compact  re-reads the tile and writes the pixel index of every
 //                   training pixel to its row of the class-major list
-//                   (block-wide scan of packed per-thread class counts);
+//                   (block-wide scan of packed per-thread class counts, then
+//                   class by class one store per training pixel);
 //   k_gather        one thread per listed pixel, all band loads in flight:
 //                   the augmented row (x_0 .. x_{B-1}, 1, 0 ..) of the
 //                   class-major training matrix (16-byte rows);
@@ -64,27 +66,12 @@ __device__ inline void load_tile(const uint8_t* __restrict__ labels, long long t
     }
 }
 
-// Byte i of 16 labels held as two 64-bit halves.
-__device__ inline uint32_t byte_at(unsigned long long lo, unsigned long long hi, int i)
-{
-    return static_cast<uint32_t>(((i < 8 ? lo : hi) >> (8 * (i & 7))) & 0xFFull);
-}
-
 // Class counters packed four to a 64-bit word (16-bit fields; a tile holds
 // 16384 labels, so no field carries into the next).
 __device__ inline unsigned int field(const unsigned long long (&v)[4], int c)
 {
     const unsigned long long w = (c < 4) ? v[0] : (c < 8) ? v[1] : (c < 12) ? v[2] : v[3];
     return static_cast<unsigned int>((w >> (16 * (c & 3))) & 0xFFFFull);
-}
-
-__device__ inline void bump(unsigned long long (&v)[4], int c)
-{
-    const unsigned long long one = 1ull << (16 * (c & 3));
-    if (c < 4) v[0] += one;
-    else if (c < 8) v[1] += one;
-    else if (c < 12) v[2] += one;
-    else v[3] += one;
 }
 
 // Block-wide exclusive scan of packed counters (`nwords` words used).
@@ -138,67 +125,79 @@ __device__ inline uint32_t byte_bits(uint32_t r)
 // classes per 64-bit word; byte compares four at a time.
 __device__ inline void count16(const uint32_t (&w)[4], int K, unsigned long long (&cnt)[4])
 {
-    #pragma unroll
-    for (int c = 0; c < MAXK; ++c) {
-        if (c < K) {
-            const uint32_t pat = static_cast<uint32_t>(c + 1) * 0x01010101u;
-            uint32_t n = 0;
-            #pragma unroll
-            for (int q = 0; q < 4; ++q) n += __popc(__vcmpeq4(w[q], pat) & 0x01010101u);
-            const unsigned long long add = static_cast<unsigned long long>(n) << (16 * (c & 3));
-            if (c < 4) cnt[0] += add; else if (c < 8) cnt[1] += add; else if (c < 12) cnt[2] += add; else cnt[3] += add;
-        }
+    // a rolled loop keeps the label passes' code small (they run it four
+    // times per thread, and instruction fetch limited them when unrolled)
+    #pragma unroll 1
+    for (int c = 0; c < K; ++c) {
+        const uint32_t pat = static_cast<uint32_t>(c + 1) * 0x01010101u;
+        uint32_t n = 0;
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) n += __popc(__vcmpeq4(w[q], pat) & 0x01010101u);
+        const unsigned long long add = static_cast<unsigned long long>(n) << (16 * (c & 3));
+        if (c < 4) cnt[0] += add; else if (c < 8) cnt[1] += add; else if (c < 12) cnt[2] += add; else cnt[3] += add;
     }
 }
 
-// Prefix sums of the per-tile class counts, class by class (run by one CTA):
-// each tile's count row becomes its first row in every class segment of the
-// class-major training list.  Also the class totals, the fit's status word and
-// the reset of the moment accumulators.
-__device__ void scan_tiles(int ntiles, int K, int B, long long cap, int any_bad, unsigned int* __restrict__ tiles,
+// Prefix sums of the per-tile class counts (run by one CTA): each tile's
+// count of class c becomes its first row within the class c segment of the
+// class-major training list (the segment's own start is added by the
+// compaction pass).  The tile rows are staged through shared memory in
+// chunks, one coalesced load and store per chunk, and scanned there with one
+// warp per class.  Also the label check, the class totals, the fit's status
+// word and the reset of the moment accumulators.
+constexpr int SCAN_CHUNK = 4096;  // words of tile rows per chunk
+
+__device__ void scan_tiles(int ntiles, int K, int B, long long cap, unsigned int* __restrict__ tiles,
                            DevModel* __restrict__ dm)
 {
-    __shared__ unsigned int woff[NW];
-    __shared__ unsigned int start;
+    __shared__ unsigned int buf[SCAN_CHUNK];
+    __shared__ unsigned int carry[MAXK];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (ntiles + TPB - 1) / TPB;
-    const int t_lo = min(ntiles, tid * per), t_hi = min(ntiles, t_lo + per);
-    if (tid == 0) start = 0u;
-    for (int c = 0; c < K; ++c) {
-        unsigned int acc = 0;
-        for (int t = t_lo; t < t_hi; ++t) acc += __ldcg(tiles + static_cast<long long>(t) * (K + 1) + c);
-        unsigned int v = acc;
-        #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int u = __shfl_up_sync(0xFFFFFFFFu, v, o);
-            if (lane >= o) v += u;
-        }
-        if (lane == 31) woff[warp] = v;
+    const int row = K + 1;
+    const int per_chunk = SCAN_CHUNK / row;
+    if (tid < K) carry[tid] = 0u;
+    int bad = 0;
+    for (int t0 = 0; t0 < ntiles; t0 += per_chunk) {
+        const int nt = min(per_chunk, ntiles - t0);
+        const int nw = nt * row;
+        const long long g0 = static_cast<long long>(t0) * row;
+        __syncthreads();  // carry set; the previous chunk's buf written out
+        for (int i = tid; i < nw; i += TPB) buf[i] = __ldcg(tiles + g0 + i);
         __syncthreads();
-        unsigned int before = 0, all = 0;
-        #pragma unroll
-        for (int w2 = 0; w2 < NW; ++w2) {
-            before += (w2 < warp) ? woff[w2] : 0u;
-            all += woff[w2];
-        }
-        unsigned int run = start + before + v - acc;
-        for (int t = t_lo; t < t_hi; ++t) {
-            unsigned int* cell = tiles + static_cast<long long>(t) * (K + 1) + c;
-            const unsigned int n = __ldcg(cell);
-            *cell = run;
-            run += n;
+        for (int t = tid; t < nt; t += TPB) bad |= buf[t * row + K] != 0u;
+        const int per = (nt + 31) / 32;
+        const int a = min(nt, lane * per), e = min(nt, a + per);
+        for (int c = warp; c < K; c += NW) {
+            unsigned int acc = 0;
+            for (int t = a; t < e; ++t) acc += buf[t * row + c];
+            unsigned int v = acc;
+            #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+                if (lane >= o) v += u;
+            }
+            unsigned int run = carry[c] + v - acc;
+            for (int t = a; t < e; ++t) {
+                const unsigned int n = buf[t * row + c];
+                buf[t * row + c] = run;
+                run += n;
+            }
+            __syncwarp();
+            if (lane == 31) carry[c] += v;
         }
         __syncthreads();
-        if (tid == 0) {
-            dm->cls_count[c] = all;
-            start += all;
-        }
-        __syncthreads();
+        for (int i = tid; i < nw; i += TPB) tiles[g0 + i] = buf[i];
     }
+    bad = __syncthreads_or(bad);
     if (tid == 0) {
+        unsigned long long total = 0;
+        for (int c = 0; c < K; ++c) {
+            dm->cls_count[c] = carry[c];
+            total += carry[c];
+        }
         int st = CVA_OK;
-        if (any_bad) st = CVA_ERR_LABEL_RANGE;
-        else if (static_cast<unsigned long long>(start) > static_cast<unsigned long long>(cap)) st = CVA_ERR_CAPACITY;
+        if (bad) st = CVA_ERR_LABEL_RANGE;
+        else if (total > static_cast<unsigned long long>(cap)) st = CVA_ERR_CAPACITY;
         dm->status = st;
         dm->fitted = 0;
         dm->tile_ticket = 0u;
@@ -265,10 +264,7 @@ __device__ __forceinline__ void tile_count_body(const uint8_t* __restrict__ labe
     __syncthreads();
     if (!last) return;
     __threadfence();
-    int any_bad = 0;
-    for (int t = tid; t < ntiles; t += TPB) any_bad |= __ldcg(tiles + static_cast<long long>(t) * (K + 1) + K) != 0u;
-    any_bad = __syncthreads_or(any_bad);
-    scan_tiles(ntiles, K, B, cap, any_bad, tiles, dm);
+    scan_tiles(ntiles, K, B, cap, tiles, dm);
 }
 
 __global__ void __launch_bounds__(TPB)
@@ -278,8 +274,22 @@ k_tile_count(const uint8_t* __restrict__ labels, long long P, int K, int B, int 
     tile_count_body(labels, P, K, B, vec, cap, ntiles, tiles, dm, blockIdx.x);
 }
 
+// Adds k to the 16-bit class counter c of packed counters v.
+__device__ inline void bump_by(unsigned long long (&v)[4], int c, unsigned int k)
+{
+    const unsigned long long add = static_cast<unsigned long long>(k) << (16 * (c & 3));
+    if (c < 4) v[0] += add;
+    else if (c < 8) v[1] += add;
+    else if (c < 12) v[2] += add;
+    else v[3] += add;
+}
+
+// One tile's training pixels written to their rows of the class-major list.
+// `cls_count` gives the class segment starts, `tiles` each tile's first row
+// within every segment.
 __device__ __forceinline__ void tile_compact_body(const uint8_t* __restrict__ labels, long long P, int K, int vec,
                                                   const unsigned int* __restrict__ tiles,
+                                                  const unsigned int* __restrict__ cls_count,
                                                   unsigned int* __restrict__ list, int tile)
 {
     __shared__ unsigned long long wsum[NW][4];
@@ -288,34 +298,33 @@ __device__ __forceinline__ void tile_compact_body(const uint8_t* __restrict__ la
     const long long t0 = static_cast<long long>(tile) * TILE;
     uint32_t w[4][4];
     load_tile(labels, t0, P, vec, w);
-    if (tid < K) base[tid] = tiles[static_cast<long long>(tile) * (K + 1) + tid];
-    const uint32_t kpat = static_cast<uint32_t>(K) * 0x01010101u;
-    // training-label masks (nonzero and <= K) and per-class counts of the 64 labels
-    uint32_t mask[4];
+    if (tid < K) {
+        unsigned int start = 0;
+        for (int c = 0; c < tid; ++c) start += cls_count[c];
+        base[tid] = start + tiles[static_cast<long long>(tile) * (K + 1) + tid];
+    }
     unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
     #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        mask[u] = 0u;
-        if ((w[u][0] | w[u][1] | w[u][2] | w[u][3]) != 0u) {
-            #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                mask[u] |= byte_bits(~__vcmpeq4(w[u][q], 0u) & ~__vcmpgtu4(w[u][q], kpat)) << (4 * q);
-            count16(w[u], K, cnt);
-        }
-    }
+    for (int u = 0; u < 4; ++u)
+        if ((w[u][0] | w[u][1] | w[u][2] | w[u][3]) != 0u) count16(w[u], K, cnt);
     unsigned long long excl[4], total[4];
     block_scan_packed(cnt, (K + 3) >> 2, wsum, excl, total);  // also orders base[] before its reads
+    // class by class: the 16-bit mask of the group's labels equal to c + 1,
+    // then one store per set bit to consecutive rows
     #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        if (!mask[u]) continue;
-        const unsigned long long l64 = w[u][0] | (static_cast<unsigned long long>(w[u][1]) << 32);
-        const unsigned long long h64 = w[u][2] | (static_cast<unsigned long long>(w[u][3]) << 32);
-        const long long p0 = t0 + u * SUB + 16LL * tid;
-        for (uint32_t m = mask[u]; m; m &= m - 1) {
-            const int i = __ffs(m) - 1;
-            const int c = static_cast<int>(byte_at(l64, h64, i)) - 1;
-            list[base[c] + field(excl, c)] = static_cast<unsigned int>(p0 + i);
-            bump(excl, c);
+        if ((w[u][0] | w[u][1] | w[u][2] | w[u][3]) == 0u) continue;
+        const unsigned int p0 = static_cast<unsigned int>(t0 + u * SUB + 16LL * tid);
+        #pragma unroll 1
+        for (int c = 0; c < K; ++c) {
+            const uint32_t pat = static_cast<uint32_t>(c + 1) * 0x01010101u;
+            uint32_t m = 0u;
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) m |= byte_bits(__vcmpeq4(w[u][q], pat)) << (4 * q);
+            if (!m) continue;
+            unsigned int pos = base[c] + field(excl, c);
+            bump_by(excl, c, __popc(m));
+            for (; m; m &= m - 1) list[pos++] = p0 + static_cast<unsigned int>(__ffs(m) - 1);
         }
     }
 }
@@ -326,7 +335,7 @@ k_tile_compact(const uint8_t* __restrict__ labels, long long P, int K, int vec,
                const DevModel* __restrict__ dm)
 {
     if (dm->status != 0) return;
-    tile_compact_body(labels, P, K, vec, tiles, list, blockIdx.x);
+    tile_compact_body(labels, P, K, vec, tiles, dm->cls_count, list, blockIdx.x);
 }
 
 // The augmented row (x_0 .. x_{B-1}, 1, 0 ..) of listed training pixel i,
@@ -464,16 +473,23 @@ __device__ __forceinline__ void moments_unit(uint16_t* XT, float* Cs, const uint
     // Gram matrix of the split unit, one 16 x 8 output tile per warp at a time
     for (int t = warp; t < MT * NTL; t += NW) {
         const int mt = t / NTL, nt = t - (t / NTL) * NTL;
-        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        // two independent accumulator chains (even and odd k steps); both
+        // hold integers below 2^24, so their sum is exact as well
+        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f}, e[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         const uint16_t* arow = XT + (mt * 16 + (lane & 15)) * UPAD + ((lane >> 4) << 3);
         const uint16_t* brow = XT + (nt * 8 + (lane & 7)) * UPAD + (((lane >> 3) & 1) << 3);
         #pragma unroll 4
-        for (int ks = 0; ks < UNIT / 16; ++ks) {
-            uint32_t af[4], bfr[2];
+        for (int ks = 0; ks < UNIT / 16; ks += 2) {
+            uint32_t af[4], bfr[2], ag[4], bg[2];
             ldsm_x4(af, arow + ks * 16);
             ldsm_x2(bfr, brow + ks * 16);
+            ldsm_x4(ag, arow + ks * 16 + 16);
+            ldsm_x2(bg, brow + ks * 16 + 16);
             mma_bf16_16816(d, af, bfr);
+            mma_bf16_16816(e, ag, bg);
         }
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) d[i] = __fadd_rn(d[i], e[i]);
         const int r0 = mt * 16 + (lane >> 2), c0 = nt * 8 + (lane & 3) * 2;
         Cs[r0 * F2 + c0] = d[0];
         Cs[r0 * F2 + c0 + 1] = d[1];
@@ -563,14 +579,9 @@ k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevMode
 // Batched form: the same passes over the flattened work of many pages.
 // ---------------------------------------------------------------------------
 
-__device__ inline int page_of_tile(const PageDev* pages, int n, unsigned long long t)
+__global__ void __launch_bounds__(TPB) kb_tile_count(const PageDev* __restrict__ pages, const int* __restrict__ tile_page)
 {
-    return find_page(pages, n, t, [](const PageDev& q) { return static_cast<unsigned long long>(q.tile0); });
-}
-
-__global__ void __launch_bounds__(TPB) kb_tile_count(const PageDev* __restrict__ pages, int n)
-{
-    const int p = page_of_tile(pages, n, blockIdx.x);
+    const int p = tile_page[blockIdx.x];
     const PageDev& pg = pages[p];
     // the training capacity is checked by the pool scan, over the whole batch
     tile_count_body(pg.labels, pg.P, pg.K, pg.B, pg.vec, 0x7FFFFFFFFFFFFFFFll, pg.ntiles, pg.tiles, pg.dm,
@@ -578,12 +589,13 @@ __global__ void __launch_bounds__(TPB) kb_tile_count(const PageDev* __restrict__
 }
 
 __global__ void __launch_bounds__(TPB)
-kb_tile_compact(const PageDev* __restrict__ pages, int n, unsigned int* __restrict__ list_pool)
+kb_tile_compact(const PageDev* __restrict__ pages, const int* __restrict__ tile_page,
+                unsigned int* __restrict__ list_pool)
 {
-    const int p = page_of_tile(pages, n, blockIdx.x);
+    const int p = tile_page[blockIdx.x];
     const PageDev& pg = pages[p];
     if (pg.dm->status != 0) return;
-    tile_compact_body(pg.labels, pg.P, pg.K, pg.vec, pg.tiles, list_pool + pg.row0,
+    tile_compact_body(pg.labels, pg.P, pg.K, pg.vec, pg.tiles, pg.dm->cls_count, list_pool + pg.row0,
                       static_cast<int>(blockIdx.x - pg.tile0));
 }
 
@@ -620,27 +632,44 @@ kb_moments(const PageDev* __restrict__ pages, int n, const BatchTotals* __restri
 
     unsigned long long acc[3] = {0ull, 0ull, 0ull};
     int cur_page = -1, cur_class = -1, cur_b = -1;
+    // each CTA takes a contiguous run of units, so it seldom changes page or class
     const unsigned long long nunits = tot->units;
-    for (unsigned long long u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const unsigned long long per = (nunits + gridDim.x - 1) / gridDim.x;
+    const unsigned long long u_end = min(nunits, (blockIdx.x + 1ull) * per);
+    // thread 0 keeps the current class's unit range and looks the page and
+    // class up again only when a unit leaves it
+    int c_page = -1, c_class = 0, c_skip = 1;
+    unsigned long long c_u0 = 0, c_u1 = 0;
+    unsigned int c_row = 0, c_nc = 0;
+    for (unsigned long long u = blockIdx.x * per; u < u_end; ++u) {
         if (tid == 0) {
-            const int p = find_page(pages, n, u, [](const PageDev& q) { return q.unit0; });
-            const PageDev& pg = pages[p];
-            unsigned long long lu = u - pg.unit0;
-            unsigned int row = 0;
-            int c = 0;
-            for (; c < pg.K; ++c) {
-                const unsigned int nc = pg.dm->cls_count[c];
-                const unsigned long long nu = (nc + UNIT - 1) / UNIT;
-                if (lu < nu) break;
-                lu -= nu;
-                row += nc;
+            if (c_page < 0 || u < c_u0 || u >= c_u1) {
+                const int p = find_page(pages, n, u, [](const PageDev& q) { return q.unit0; });
+                const PageDev& pg = pages[p];
+                unsigned long long lu = u - pg.unit0;
+                unsigned int row = 0, nc = 0;
+                int c = 0;
+                for (; c < pg.K; ++c) {
+                    nc = pg.dm->cls_count[c];
+                    const unsigned long long nu = (nc + UNIT - 1) / UNIT;
+                    if (lu < nu) break;
+                    lu -= nu;
+                    row += nc;
+                }
+                c_page = p;
+                c_class = c;
+                c_skip = pg.dm->status != 0 || c >= pg.K;
+                c_u0 = u - lu;
+                c_u1 = c >= pg.K ? u + 1 : c_u0 + (nc + UNIT - 1) / UNIT;
+                c_row = row;
+                c_nc = c >= pg.K ? 0u : nc;
             }
-            const unsigned int row0 = row + static_cast<unsigned int>(lu) * UNIT;
-            s_page = p;
-            s_class = c;
+            const unsigned int row0 = c_row + static_cast<unsigned int>(u - c_u0) * UNIT;
+            s_page = c_page;
+            s_class = c_class;
             s_row0 = row0;
-            s_len = static_cast<int>(min(static_cast<unsigned int>(UNIT), row + pg.dm->cls_count[c < pg.K ? c : 0] - row0));
-            s_skip = pg.dm->status != 0 || c >= pg.K;
+            s_len = c_skip ? 0 : static_cast<int>(min(static_cast<unsigned int>(UNIT), c_row + c_nc - row0));
+            s_skip = c_skip;
         }
         __syncthreads();
         const int p = s_page, c = s_class;
@@ -700,16 +729,17 @@ cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const u
 
 namespace cva {
 
-cudaError_t launch_batch_tile_count(const PageDev* pages, int n, long long ntiles_total, cudaStream_t s)
+cudaError_t launch_batch_tile_count(const PageDev* pages, const int* tile_page, long long ntiles_total,
+                                    cudaStream_t s)
 {
-    kb_tile_count<<<static_cast<unsigned>(ntiles_total), TPB, 0, s>>>(pages, n);
+    kb_tile_count<<<static_cast<unsigned>(ntiles_total), TPB, 0, s>>>(pages, tile_page);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_tile_compact(const PageDev* pages, int n, long long ntiles_total, unsigned int* list_pool,
-                                      cudaStream_t s)
+cudaError_t launch_batch_tile_compact(const PageDev* pages, const int* tile_page, long long ntiles_total,
+                                      unsigned int* list_pool, cudaStream_t s)
 {
-    kb_tile_compact<<<static_cast<unsigned>(ntiles_total), TPB, 0, s>>>(pages, n, list_pool);
+    kb_tile_compact<<<static_cast<unsigned>(ntiles_total), TPB, 0, s>>>(pages, tile_page, list_pool);
     return cudaGetLastError();
 }
 

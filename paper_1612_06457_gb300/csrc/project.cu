@@ -342,9 +342,19 @@ kb_train_range(const PageDev* __restrict__ pages, int n, const BatchTotals* __re
     __shared__ ProjSmem<KV> sm;
     float mn[KV], mx[KV];
     int cur = -1;
+    // each CTA takes a contiguous run of items, so it seldom changes page
     const unsigned long long nitems = tot->titems;
-    for (unsigned long long it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int p = find_page(pages, n, it, [](const PageDev& q) { return q.titem0; });
+    const unsigned long long per = (nitems + gridDim.x - 1) / gridDim.x;
+    const unsigned long long it_end = min(nitems, (blockIdx.x + 1ull) * per);
+    unsigned long long r0 = 0, r1 = 0;  // items of the current page
+    int p = 0;
+    for (unsigned long long it = blockIdx.x * per; it < it_end; ++it) {
+        if (it < r0 || it >= r1) {
+            p = find_page(pages, n, it, [](const PageDev& q) { return q.titem0; });
+            r0 = pages[p].titem0;
+            r1 = r0 + (pages[p].nrows + BATCH_ROWS_PER_ITEM - 1) / BATCH_ROWS_PER_ITEM;
+            if (r1 <= it) r1 = it + 1;
+        }
         const PageDev& pg = pages[p];
         if (pg.dm->status != 0 || !pg.dm->fitted) continue;
         if (p != cur) {
@@ -366,14 +376,24 @@ kb_train_range(const PageDev* __restrict__ pages, int n, const BatchTotals* __re
 
 template <int KV>
 __global__ void __launch_bounds__(TPB, 2)
-kb_project_v8(const PageDev* __restrict__ pages, int n, long long nitems, int gpi)
+kb_project_v8(const PageDev* __restrict__ pages, const int* __restrict__ item_page, long long it_begin,
+              long long it_end, int gpi, int contiguous)
 {
     __shared__ ProjSmem<KV> sm;
     float mn[KV], mx[KV];
     int cur = -1;
-    for (long long it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int p = find_page(pages, n, static_cast<unsigned long long>(it),
-                                [](const PageDev& q) { return static_cast<unsigned long long>(q.item0); });
+    // persistent CTAs take contiguous runs of items (few page changes);
+    // otherwise one CTA per item
+    long long it0 = it_begin + blockIdx.x, it1 = it_end, step = gridDim.x;
+    if (contiguous) {
+        const long long nitems = it_end - it_begin;
+        const long long per = (nitems + gridDim.x - 1) / gridDim.x;
+        it0 = it_begin + static_cast<long long>(blockIdx.x) * per;
+        it1 = it0 + per < it_end ? it0 + per : it_end;
+        step = 1;
+    }
+    for (long long it = it0; it < it1; it += step) {
+        const int p = item_page[it];
         const PageDev& pg = pages[p];
         if (pg.dm->status != 0 || !pg.dm->fitted) continue;
         if (p != cur) {
@@ -569,21 +589,23 @@ cudaError_t launch_batch_train_range(const PageDev* pages, int n, const BatchTot
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_project(const PageDev* pages, int n, long long items_total, int groups_per_item,
-                                 int grid, int max_k, cudaStream_t s)
+cudaError_t launch_batch_project(const PageDev* pages, const int* item_page, long long it_begin, long long it_end,
+                                 int groups_per_item, int grid, int k, cudaStream_t s)
 {
-    if (items_total < 1) return cudaSuccess;
-    const long long g = grid < items_total ? grid : items_total;
+    const long long items = it_end - it_begin;
+    if (items < 1) return cudaSuccess;
+    const long long g = grid < items ? grid : items;
+    const int contiguous = g < items ? 1 : 0;
     const unsigned gx = static_cast<unsigned>(g);
-    switch (max_k) {
-        case 1: kb_project_v8<1><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
-        case 2: kb_project_v8<2><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
-        case 3: kb_project_v8<3><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
-        case 4: kb_project_v8<4><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
-        case 5: kb_project_v8<5><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
-        case 6: kb_project_v8<6><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
-        case 7: kb_project_v8<7><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
-        case 8: kb_project_v8<8><<<gx, TPB, 0, s>>>(pages, n, items_total, groups_per_item); break;
+    switch (k) {
+        case 1: kb_project_v8<1><<<gx, TPB, 0, s>>>(pages, item_page, it_begin, it_end, groups_per_item, contiguous); break;
+        case 2: kb_project_v8<2><<<gx, TPB, 0, s>>>(pages, item_page, it_begin, it_end, groups_per_item, contiguous); break;
+        case 3: kb_project_v8<3><<<gx, TPB, 0, s>>>(pages, item_page, it_begin, it_end, groups_per_item, contiguous); break;
+        case 4: kb_project_v8<4><<<gx, TPB, 0, s>>>(pages, item_page, it_begin, it_end, groups_per_item, contiguous); break;
+        case 5: kb_project_v8<5><<<gx, TPB, 0, s>>>(pages, item_page, it_begin, it_end, groups_per_item, contiguous); break;
+        case 6: kb_project_v8<6><<<gx, TPB, 0, s>>>(pages, item_page, it_begin, it_end, groups_per_item, contiguous); break;
+        case 7: kb_project_v8<7><<<gx, TPB, 0, s>>>(pages, item_page, it_begin, it_end, groups_per_item, contiguous); break;
+        case 8: kb_project_v8<8><<<gx, TPB, 0, s>>>(pages, item_page, it_begin, it_end, groups_per_item, contiguous); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
