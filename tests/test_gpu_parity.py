@@ -327,3 +327,47 @@ def test_training_capacity_is_checked_on_device():
     n, mc, Sw, Sb = cva.cva_model_get_scatter(m)
     assert n.tolist() == [H * W - H * ((W + 1) // 2), H * ((W + 1) // 2)]
     m.close()
+
+
+def test_large_cube_23b_8192x6144_K6():
+    """23 bands, 8192 x 6144 (50 M pixels, 2.3 GB), 6 classes with 1 M down to
+    5 k training pixels, 5 variates: the fit in full against the oracle, the
+    fused 8-bit projection and the FP32 projection on sampled row bands (the
+    oracle's training range from the scores of all training pixels)."""
+    _skip_without_gpu()
+    w = named_workload("cube23b_8192x6144_K6")
+    ref = oracle.fit(w.cube, w.labels, w.K)
+    m, cube, labels, g = _gpu_fit(w, nvec=w.k)
+    _check_fit(g, ref, w.K, w.B, w.k)
+    out = torch.empty((w.k, w.H, w.W), dtype=torch.uint8, device=DEV)
+    cva.cva_project_u8(cube, m, w.k, cva.CVA_RANGE_TRAINING, out)
+    y = torch.empty((w.k, w.H, w.W), dtype=torch.float32, device=DEV)
+    cva.cva_project(cube, m, w.k, out_f32=y)
+    lab = np.flatnonzero(w.labels.reshape(-1))
+    sub = w.cube.reshape(w.B, -1)[:, lab]
+    y_tr = oracle.project(sub.reshape(w.B, 1, -1), ref["V"], ref["mu"], w.k)
+    rng = oracle.range_global(y_tr)
+    u = out.reshape(w.k, -1)
+    yy = y.reshape(w.k, -1)
+    for r0 in (0, w.H // 2 - 32, w.H - 64):
+        p0, p1 = r0 * w.W, (r0 + 64) * w.W
+        y_ref = oracle.project(w.cube, ref["V"], ref["mu"], w.k, p0, p1)
+        uref = oracle.to_u8(y_ref, rng)
+        assert _u8_ok(u[:, p0:p1].cpu().numpy(), uref) >= 0.999
+        assert _normwise(yy[:, p0:p1].cpu().numpy(), y_ref) <= 1e-4
+    m.close()
+
+
+def test_output_only_4_byte_aligned():
+    """An 8-bit output buffer that is 4- but not 8-byte aligned takes the
+    scalar projection path and gives the same image."""
+    _skip_without_gpu()
+    w = make_workload(113, 10, 96, 128, 3, (500, 400, 300), 2, separation=(1.0, 3.0))
+    m, cube, labels, g = _gpu_fit(w, nvec=2)
+    o1 = torch.empty((2, w.H, w.W), dtype=torch.uint8, device=DEV)
+    base = torch.empty(2 * w.P + 16, dtype=torch.uint8, device=DEV)
+    o2 = base[4:4 + 2 * w.P].view(2, w.H, w.W)
+    cva.cva_project_u8(cube, m, 2, cva.CVA_RANGE_TRAINING, o1)
+    cva.cva_project_u8(cube, m, 2, cva.CVA_RANGE_TRAINING, o2)
+    assert torch.equal(o1, o2)
+    m.close()
