@@ -70,6 +70,10 @@ def _load():
         lib.orc_range_global.argtypes = [P, I64, I64, P]
         lib.orc_range_training.argtypes = [P, I64, I64, P, P]
         lib.orc_to_u8.argtypes = [P, I64, I64, P, P]
+        lib.orc_to_u16.argtypes = [P, I64, I64, P, P]
+        lib.orc_to_u16.restype = None
+        lib.orc_percentile_range.argtypes = [P, I64, I64, I64, P]
+        lib.orc_percentile_range.restype = ctypes.c_int
         for name in ("orc_class_sums", "orc_scatter", "orc_gen_eig", "orc_project"):
             getattr(lib, name).restype = ctypes.c_int
         for name in ("orc_range_global", "orc_range_training", "orc_to_u8"):
@@ -196,3 +200,39 @@ def to_u8(y: np.ndarray, rng: np.ndarray) -> np.ndarray:
     out = np.zeros((k, P), np.uint8)
     lib.orc_to_u8(_ptr(y), k, P, _ptr(rng), _ptr(out))
     return out
+
+
+def to_u16(y: np.ndarray, rng: np.ndarray) -> np.ndarray:
+    """floor(65535 (y - lo) / (hi - lo) + 1/2) clamped to 0..65535: the 16-bit
+    image of the same rescale (Section 2's CVA-GSL tool writes 8- and 16-bit
+    images)."""
+    lib = _load()
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    k, P = y.shape
+    rng = np.ascontiguousarray(rng, dtype=np.float64)
+    out = np.zeros((k, P), np.uint16)
+    lib.orc_to_u16(_ptr(y), k, P, _ptr(rng), _ptr(out))
+    return out
+
+
+def percentile_basis_points(percent: float) -> int:
+    """p percent as an integer number of 0.01 % steps (0 .. 4999)."""
+    bp = int(round(percent * 100.0))
+    if abs(bp - percent * 100.0) > 1e-6 or not 0 <= bp <= 4999:
+        raise ValueError("percent must be a multiple of 0.01 in [0, 50)")
+    return bp
+
+
+def percentile_range(y: np.ndarray, percent: float) -> np.ndarray:
+    """The third rescale of Section 2: (lo_j, hi_j) with `percent` of the
+    pixels taken out of each tail -- m = floor(p P / 100) values at each end,
+    lo the (m+1)-th smallest, hi the (m+1)-th largest.  Values are elements of
+    y (float32 input gives float32-representable results)."""
+    lib = _load()
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    k, P = y.shape
+    r = np.zeros(2 * k)
+    rc = lib.orc_percentile_range(_ptr(y), k, P, percentile_basis_points(percent), _ptr(r))
+    if rc != 0:
+        raise OracleError(rc, "orc_percentile_range")
+    return r

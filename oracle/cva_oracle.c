@@ -37,7 +37,12 @@
  *     return opposite signs);
  *   - projections are centred on the training mean: y_j = v_j^T (x - mu);
  *   - the 8-bit value is floor(255 (y - lo) / (hi - lo) + 1/2) clamped to
- *     0..255, and 0 everywhere when hi <= lo;
+ *     0..255, and 0 everywhere when hi <= lo; the 16-bit value (Section 2's
+ *     CVA-GSL tool writes 8- and 16-bit images) the same with 65535;
+ *   - the third rescale takes p percent of the pixels out of EACH tail:
+ *     with m = floor(p P / 100), lo is the (m+1)-th smallest and hi the
+ *     (m+1)-th largest value of the projection, p in steps of 0.01 below 50
+ *     (the paper's values are 0.01, 0.1, 1 and 5);
  *   - Sw is "not positive definite" when a Cholesky pivot falls to or below
  *     1e-12 times its own diagonal entry of Sw; no ridge is added.
  *
@@ -372,4 +377,47 @@ void orc_to_u8(const double* y, int64_t k, int64_t P, const double* range, uint8
             out[j * P + p] = (uint8_t)v;
         }
     }
+}
+
+
+/* out[j * P + p] = clamp(floor(65535 (y - lo) / (hi - lo) + 1/2), 0, 65535). */
+void orc_to_u16(const double* y, int64_t k, int64_t P, const double* range, uint16_t* out)
+{
+    for (int64_t j = 0; j < k; ++j) {
+        double lo = range[2 * j], hi = range[2 * j + 1];
+        for (int64_t p = 0; p < P; ++p) {
+            double v = 0.0;
+            if (hi > lo) v = floor(65535.0 * (y[j * P + p] - lo) / (hi - lo) + 0.5);
+            if (v < 0.0) v = 0.0;
+            if (v > 65535.0) v = 65535.0;
+            out[j * P + p] = (uint16_t)v;
+        }
+    }
+}
+
+static int cmp_double(const void* a, const void* b)
+{
+    const double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* The third rescale's range (Section 2: "taking out" a percentile of the
+ * data): with bp = p * 100 (p in percent, steps of 0.01, p < 50) and
+ * m = floor(bp P / 10000) values taken out of each tail, lo_j is the
+ * (m+1)-th smallest and hi_j the (m+1)-th largest of the P values of
+ * projection j.  bp = 0 gives the global range. */
+int orc_percentile_range(const double* y, int64_t k, int64_t P, int64_t bp, double* range)
+{
+    if (k < 1 || P < 1 || bp < 0 || bp > 4999) return ORC_ERR_ARG;
+    double* v = (double*)malloc(sizeof(double) * (size_t)P);
+    if (!v) return ORC_ERR_ARG;
+    const int64_t m = (bp * P) / 10000;
+    for (int64_t j = 0; j < k; ++j) {
+        memcpy(v, y + j * P, sizeof(double) * (size_t)P);
+        qsort(v, (size_t)P, sizeof(double), cmp_double);
+        range[2 * j] = v[m];
+        range[2 * j + 1] = v[P - 1 - m];
+    }
+    free(v);
+    return ORC_OK;
 }

@@ -320,6 +320,62 @@ def test_ranges_global_and_training():
     np.testing.assert_array_equal(oracle.range_training(y, labels), [-2, 1, 3, 9])
 
 
+def test_to_u16_end_points_rounding_and_clamp():
+    y = np.array([[0.0, 1.0, 2.0, 3.0, -1.0, 1.0 - 1e-9, 2.0 / 65535.0]])
+    rng = np.array([0.0, 2.0])
+    u = oracle.to_u16(y, rng)[0]
+    assert u.dtype == np.uint16
+    assert u[0] == 0 and u[2] == 65535        # range ends map to 0 and 65535
+    assert u[1] == 32768                       # 32767.5 rounds half up
+    assert u[3] == 65535 and u[4] == 0         # clamped outside the range
+    assert u[5] == 32767                       # just below the half point
+    assert u[6] == 1                           # one step of the 16-bit scale
+    assert np.all(oracle.to_u16(y, np.array([1.0, 1.0])) == 0)  # empty range
+
+
+def _order_stat_by_counting(vals, m, largest):
+    """The (m+1)-th smallest (or largest) value of vals, by counting: the v
+    with at most m values strictly beyond it and more than m at or beyond it."""
+    for v in vals:
+        beyond = sum(1 for x in vals if (x > v if largest else x < v))
+        at_or_beyond = sum(1 for x in vals if (x >= v if largest else x <= v))
+        if beyond <= m < at_or_beyond:
+            return v
+    raise AssertionError("no order statistic")
+
+
+@pytest.mark.parametrize("P", [1, 2, 7, 100, 401])
+@pytest.mark.parametrize("percent", [0.0, 0.01, 0.1, 1.0, 5.0, 12.34, 49.99])
+def test_percentile_range_by_counting(P, percent):
+    """Third rescale of Section 2: p percent out of each tail.  Brute force by
+    counting on small arrays with ties (integers), against the oracle's sort."""
+    rng = np.random.default_rng(P * 7 + int(percent * 100))
+    y = rng.integers(-20, 20, size=(2, P)).astype(np.float64)
+    got = oracle.percentile_range(y, percent)
+    m = int(round(percent * 100)) * P // 10000
+    for j in range(2):
+        vals = list(y[j])
+        assert got[2 * j] == _order_stat_by_counting(vals, m, largest=False)
+        assert got[2 * j + 1] == _order_stat_by_counting(vals, m, largest=True)
+
+
+def test_percentile_range_special_cases():
+    y = np.random.default_rng(5).normal(size=(3, 1000))
+    # nothing taken out: the global range of the first rescale
+    np.testing.assert_array_equal(oracle.percentile_range(y, 0.0), oracle.range_global(y))
+    # 1 % of 1000 values out of each tail: 10 values gone at each end
+    s = np.sort(y, axis=1)
+    r = oracle.percentile_range(y, 1.0)
+    np.testing.assert_array_equal(r[0::2], s[:, 10])
+    np.testing.assert_array_equal(r[1::2], s[:, 989])
+    # 0.01 % of 1000 values is 0.1 of a value: nothing taken out
+    np.testing.assert_array_equal(oracle.percentile_range(y, 0.01), oracle.range_global(y))
+    with pytest.raises(ValueError):
+        oracle.percentile_range(y, 0.005)
+    with pytest.raises(ValueError):
+        oracle.percentile_range(y, 50.0)
+
+
 # --------------------------------------------------------------------------
 # errors
 # --------------------------------------------------------------------------
