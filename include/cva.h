@@ -82,7 +82,8 @@ typedef enum {
 typedef struct cva_model cva_model;
 
 /* Create a model for B bands and K classes on the current CUDA device.  Owns
- * until cva_model_destroy: a device block of about 150 KB, a per-tile
+ * until cva_model_destroy: a device block of about 150 KB, a 512 KB
+ * histogram block for cva_percentile_range, a per-tile
  * workspace of 0.5 MB per class, and the gathered training matrix of
  * 2 ((B + 8) & ~7) bytes per training pixel with room for
  * CVA_DEFAULT_TRAIN_CAPACITY pixels (see cva_model_reserve).  *out is set to
@@ -175,6 +176,30 @@ int cva_project(const uint16_t* cube, int B, int H, int W, cva_model* m, int k,
  *   out   device, k x H x W uint8 */
 int cva_to_u8(const float* proj, int k, int H, int W, int mode, const float* range,
               cva_model* m, uint8_t* out, void* stream);
+
+/* The third rescale's range (Section 2: the 0.01, 0.1, 1 or 5 percentiles of
+ * the projected data taken out before the same linear rescale).  With p =
+ * `percent` and m = floor(p P / 100) values taken out at EACH end of every
+ * projection, range_out[2 j] is the (m+1)-th smallest and range_out[2 j + 1]
+ * the (m+1)-th largest value of proj[j] (exact order statistics of the
+ * float32 values).  Feed it to cva_to_u8 / cva_to_u16 with CVA_RANGE_GIVEN;
+ * pixels outside the range clamp to 0 and the top code.
+ *   proj       device, k x H x W float32 (4-byte aligned)
+ *   percent    a multiple of 0.01 in [0, 50); 0 gives the global range
+ *   m          any model on this device: its scratch (a 512 KB histogram
+ *              block and 256 bytes of state) is used, so calls sharing a
+ *              model must not overlap on the GPU
+ *   range_out  device, 2 k float32
+ * Three passes over proj, asynchronous on `stream`. */
+int cva_percentile_range(const float* proj, int k, int H, int W, double percent, cva_model* m,
+                         float* range_out, void* stream);
+
+/* 16-bit image of the same rescale (the paper's C tool writes 8- and 16-bit
+ * images): out = clamp(floor(65535 (y - lo) / (hi - lo) + 1/2), 0, 65535),
+ * 0 if hi <= lo.  Arguments as for cva_to_u8; out is device k x H x W uint16
+ * (2-byte aligned). */
+int cva_to_u16(const float* proj, int k, int H, int W, int mode, const float* range,
+               cva_model* m, uint16_t* out, void* stream);
 
 /* Fused projection and 8-bit rescale: one pass over the cube for
  * CVA_RANGE_TRAINING and CVA_RANGE_GIVEN, two passes (range, then

@@ -53,6 +53,8 @@ SIGNATURES = {
     "cva_project": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P]),
     "cva_to_u8": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "cva_project_u8": (_I, [_P, _I, _I, _I, _P, _I, _I, _P, _P, _P]),
+    "cva_percentile_range": (_I, [_P, _I, _I, _I, ctypes.c_double, _P, _P, _P]),
+    "cva_to_u16": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "cva_fit_project_u8_noalloc": (_I, [_P, _I, _I, _I, _P, _I, _I, _P, _P, _P, _P]),
     "cva_batch_create": (_I, [_I, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p)]),
     "cva_batch_destroy": (None, [_P]),
@@ -333,3 +335,21 @@ def cva_batch_tune(b: Batch, pages, stream=None):
     chosen = (ctypes.c_int * 2)()
     _check(load().cva_batch_tune(b.handle, arr, len(pages), _stream_ptr(stream), chosen), "cva_batch_tune")
     return int(chosen[0]), int(chosen[1])
+
+
+def cva_percentile_range(proj: torch.Tensor, percent: float, m: Model, range_out: torch.Tensor, stream=None) -> None:
+    """(lo, hi) of each projection with ``percent`` of the pixels taken out of
+    each tail (see cva.h) into the device float32 tensor ``range_out`` (2 k)."""
+    k, H, W = proj.shape
+    _check(load().cva_percentile_range(_dptr(proj, torch.float32, "proj"), k, H, W, float(percent), m.handle,
+                                       _dptr(range_out, torch.float32, "range_out"), _stream_ptr(stream)),
+           "cva_percentile_range")
+
+
+def cva_to_u16(proj: torch.Tensor, mode: int, out: torch.Tensor, m: Optional[Model] = None,
+               range: Optional[torch.Tensor] = None, stream=None) -> None:
+    """16-bit image of the linear rescale (see cva.h)."""
+    k, H, W = proj.shape
+    _check(load().cva_to_u16(_dptr(proj, torch.float32, "proj"), k, H, W, mode,
+                             _dptr(range, torch.float32, "range"), m.handle if m is not None else None,
+                             _dptr(out, torch.uint16, "out"), _stream_ptr(stream)), "cva_to_u16")

@@ -23,7 +23,12 @@ struct cva_model {
     unsigned int* list;  // class-major training-pixel indices, cap entries
     uint16_t* xtr;       // gathered training matrix, cap rows of xtr_row(B)
     long long cap;       // training pixels `list` and `xtr` hold
+    unsigned int* hist;  // order-statistic histograms, MAXB x 2 x 2048 words (zero between calls)
 };
+
+namespace {
+constexpr size_t HIST_WORDS = static_cast<size_t>(cva::MAXB) * 2 * 2048;
+}
 
 namespace {
 
@@ -109,16 +114,19 @@ int cva_model_create(int B, int K, cva_model** out)
     unsigned int* tiles = nullptr;
     unsigned int* list = nullptr;
     uint16_t* xtr = nullptr;
+    unsigned int* hist = nullptr;
     const size_t cap = CVA_DEFAULT_TRAIN_CAPACITY;
     if (cudaMalloc(&dm, sizeof(DevModel)) != cudaSuccess) return CVA_ERR_CUDA;
     if (cudaMalloc(&tiles, sizeof(unsigned int) * static_cast<size_t>(cva::MAX_TILES) * (K + 1)) != cudaSuccess ||
         cudaMalloc(&list, sizeof(unsigned int) * cap) != cudaSuccess ||
         cudaMalloc(&xtr, sizeof(uint16_t) * cap * cva::xtr_row(B)) != cudaSuccess ||
-        cudaMemset(dm, 0, sizeof(DevModel)) != cudaSuccess) {
+        cudaMalloc(&hist, sizeof(unsigned int) * HIST_WORDS) != cudaSuccess ||
+        cudaMemset(dm, 0, sizeof(DevModel)) != cudaSuccess || cudaMemset(hist, 0, sizeof(unsigned int) * HIST_WORDS)) {
         cudaFree(dm);
         cudaFree(tiles);
         cudaFree(list);
         cudaFree(xtr);
+        cudaFree(hist);
         return CVA_ERR_CUDA;
     }
     cva_model* m = new (std::nothrow) cva_model;
@@ -127,6 +135,7 @@ int cva_model_create(int B, int K, cva_model** out)
         cudaFree(tiles);
         cudaFree(list);
         cudaFree(xtr);
+        cudaFree(hist);
         return CVA_ERR_INVALID_ARG;
     }
     m->B = B;
@@ -141,6 +150,7 @@ int cva_model_create(int B, int K, cva_model** out)
     m->tiles = tiles;
     m->list = list;
     m->xtr = xtr;
+    m->hist = hist;
     m->cap = static_cast<long long>(cap);
     *out = m;
     return CVA_OK;
@@ -174,6 +184,7 @@ void cva_model_destroy(cva_model* m)
     cudaFree(m->tiles);
     cudaFree(m->list);
     cudaFree(m->xtr);
+    cudaFree(m->hist);
     delete m;
 }
 
@@ -337,6 +348,62 @@ int cva_to_u8(const float* proj, int k, int H, int W, int mode, const float* ran
             e = cva::launch_f32_to_u8(proj, k, P, dmc, range, out, sms, s);
             break;
         }
+        default:
+            return CVA_ERR_INVALID_ARG;
+    }
+    return from_cuda(e);
+}
+
+int cva_percentile_range(const float* proj, int k, int H, int W, double percent, cva_model* m, float* range_out,
+                         void* stream)
+{
+    if (!m || k < 1 || k > CVA_MAX_BANDS || H < 1 || W < 1) return CVA_ERR_INVALID_ARG;
+    const long long P = static_cast<long long>(H) * W;
+    if (P >= (1LL << 31)) return CVA_ERR_INVALID_ARG;
+    const double scaled = percent * 100.0;
+    if (!(scaled >= -1e-6 && scaled < 4999.5)) return CVA_ERR_INVALID_ARG;
+    const long long bp = static_cast<long long>(scaled + 0.5);
+    if (scaled - static_cast<double>(bp) > 1e-6 || static_cast<double>(bp) - scaled > 1e-6) return CVA_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(proj) % 4 != 0 || reinterpret_cast<uintptr_t>(range_out) % 4 != 0)
+        return CVA_ERR_INVALID_ARG;
+    if (!device_visible(proj) || !device_visible(range_out)) return CVA_ERR_INVALID_ARG;
+    const long long mt = (bp * P) / 10000;
+    return from_cuda(cva::launch_percentile_range(proj, k, P, mt, m->dm, m->hist, range_out, m->num_sms,
+                                                  static_cast<cudaStream_t>(stream)));
+}
+
+int cva_to_u16(const float* proj, int k, int H, int W, int mode, const float* range, cva_model* m, uint16_t* out,
+               void* stream)
+{
+    if (k < 1 || k > CVA_MAX_BANDS || H < 1 || W < 1 || static_cast<long long>(H) * W >= (1LL << 31))
+        return CVA_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(proj) % 4 != 0 || reinterpret_cast<uintptr_t>(out) % 2 != 0)
+        return CVA_ERR_INVALID_ARG;
+    if (!device_visible(proj) || !device_visible(out)) return CVA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long P = static_cast<long long>(H) * W;
+    cudaError_t e = cudaSuccess;
+    int sms = 0, dev = 0;
+    if (m) sms = m->num_sms;
+    else if (cudaGetDevice(&dev) != cudaSuccess ||
+             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    switch (mode) {
+        case CVA_RANGE_GLOBAL:
+            if (!m) return CVA_ERR_INVALID_ARG;
+            e = cva::launch_range_init(m->dm->work_range, k, s);
+            if (e == cudaSuccess) e = cva::launch_f32_range(proj, k, P, m->dm, m->dm->work_range, sms, s);
+            if (e == cudaSuccess) e = cva::launch_f32_to_u16(proj, k, P, m->dm->work_range, out, sms, s);
+            break;
+        case CVA_RANGE_TRAINING:
+            if (!m || k > m->fit_nvec) return CVA_ERR_INVALID_ARG;
+            e = cva::launch_f32_to_u16(proj, k, P, m->dm->train_range, out, sms, s);
+            break;
+        case CVA_RANGE_GIVEN:
+            if (!range || !device_visible(range) || reinterpret_cast<uintptr_t>(range) % 4 != 0)
+                return CVA_ERR_INVALID_ARG;
+            e = cva::launch_f32_to_u16(proj, k, P, range, out, sms, s);
+            break;
         default:
             return CVA_ERR_INVALID_ARG;
     }

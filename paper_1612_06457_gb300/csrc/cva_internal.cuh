@@ -94,6 +94,10 @@ struct DevModel {
     // of ord_enc, so that integer atomics give the extremes.
     unsigned long long train_enc64[2 * MAXB];  // over the training pixels
     unsigned long long work_enc64[2 * MAXB];   // scratch for range passes
+
+    // ---- order statistics of the third rescale ------------------------------
+    unsigned int sel_prefix[2 * MAXB];  // known leading key bits of (lo, hi) of each variate
+    unsigned int sel_rank[2 * MAXB];    // rank still to find among the keys with that prefix
 };
 
 // -------------------------------------------------------------------------
@@ -127,6 +131,14 @@ cudaError_t launch_f32_range(const float* proj, int k, long long P, const DevMod
                              float* range_acc, int num_sms, cudaStream_t s);
 cudaError_t launch_f32_to_u8(const float* proj, int k, long long P, const DevModel* dm,
                              const float* range, uint8_t* out, int num_sms, cudaStream_t s);
+
+// Third rescale: lo / hi of each of k projections with m values taken out of
+// each tail (`hist`: 2 x 2048 words per variate, zero on entry and on exit).
+cudaError_t launch_percentile_range(const float* proj, int k, long long P, long long m, DevModel* dm,
+                                    unsigned int* hist, float* range_out, int num_sms, cudaStream_t s);
+// 16-bit rescale of k float32 projections with the (lo, hi) pairs in `range`.
+cudaError_t launch_f32_to_u16(const float* proj, int k, long long P, const float* range, uint16_t* out,
+                              int num_sms, cudaStream_t s);
 
 // FP64 form: the training range in FP64 (into dm->train_enc64), and the
 // projection with FP64 coefficients and accumulation.  The 8-bit range comes
