@@ -277,6 +277,50 @@ def _precision_forms(cva, torch, w, m, cube, labels, out, stream, steps=5):
     return res
 
 
+def _time_calls(torch, fn, stream, reps=20):
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            fn()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _other_outputs(cva, torch, w, m, cube, stream, peak):
+    """The other image paths on the same cube, each timed alone: the FP32
+    projection, the third rescale's trimmed range (1 % out of each tail, three
+    passes over the projections), and the 8- and 16-bit rescales from FP32."""
+    P, k = w.P, w.k
+    y = torch.empty((k, w.H, w.W), dtype=torch.float32, device=cube.device)
+    r = torch.empty(2 * k, dtype=torch.float32, device=cube.device)
+    u8 = torch.empty((k, w.H, w.W), dtype=torch.uint8, device=cube.device)
+    u16 = torch.empty((k, w.H, w.W), dtype=torch.uint16, device=cube.device)
+    res = {}
+
+    def entry(name, ms, nbytes):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        res[name] = {"ms": ms, "alg_bytes": nbytes, "GB/s": gbs, "frac_of_hbm": gbs / peak}
+
+    entry("project_f32", _time_calls(torch, lambda: cva.cva_project(cube, m, k, out_f32=y, stream=stream), stream),
+          P * (2 * w.B + 4 * k))
+    entry("percentile_range_1pct", _time_calls(torch, lambda: cva.cva_percentile_range(y, 1.0, m, r, stream=stream),
+                                               stream), 3 * 4 * k * P)
+    entry("to_u8_given", _time_calls(torch, lambda: cva.cva_to_u8(y, cva.CVA_RANGE_GIVEN, u8, range=r, stream=stream),
+                                     stream), 5 * k * P)
+    entry("to_u16_given", _time_calls(torch, lambda: cva.cva_to_u16(y, cva.CVA_RANGE_GIVEN, u16, range=r,
+                                                                     stream=stream), stream), 6 * k * P)
+    t = res["project_f32"]["ms"] + res["percentile_range_1pct"]["ms"] + res["to_u8_given"]["ms"]
+    res["third_rescale_u8_image_mpixel_s"] = P / (t * 1e-3) / 1e6
+    return res
+
+
 def _errors_vs_oracle(cva, torch, w, m, cube, out, keep, stream):
     """Eigenvalues, canonical vectors (S_w norm), projections and codes of the
     mixed form against the FP64 oracle (projection rows: the oracle's sample)."""
@@ -426,6 +470,7 @@ def run_ours(a):
     precision = None
     if rank == 0 and not a.no_precision:
         precision = _precision_forms(cva, torch, w, m, cube, labels, out, stream)
+    others = _other_outputs(cva, torch, w, m, cube, stream, _peaks()[0]) if rank == 0 and not a.no_precision else None
 
     if rank == 0:
         peak, peak_kind = _peaks()
@@ -452,6 +497,7 @@ def run_ours(a):
             "clocks": clocks,
             "fit_ms": ms - proj_ms,
             "precision": precision,
+            "other_outputs": others,
         }
         if not a.no_cpu_baseline and world == 1:
             rows = max(1, min(w.H, 256 * 4096 // max(w.W, 1)))

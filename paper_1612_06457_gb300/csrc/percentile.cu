@@ -10,8 +10,8 @@
 // next digit of the keys that match the target's known prefix, then one CTA
 // per variate finds the bin holding the target's rank and extends the prefix.
 // Every pass reads the projections once (HBM-bound); the histograms are
-// privatized in shared memory with warp-aggregated atomics (many keys share
-// the leading digits).
+// privatized in shared memory (per warp in the first pass, where every key
+// counts and many share the leading digits).
 #include "cva_internal.cuh"
 
 namespace cva {
@@ -54,34 +54,33 @@ __global__ void k_sel_init(DevModel* __restrict__ dm, int k, unsigned int m, uns
     }
 }
 
+// Passes 1 and 2: only keys that match a target's prefix are counted (few),
+// into that target's shared histogram.
 template <int S>
-__device__ inline void count_key(uint32_t key, uint32_t p_lo, uint32_t p_hi, unsigned int (*h)[NBIN])
+__device__ inline void count_key(uint32_t key, uint32_t p_lo, uint32_t p_hi, unsigned int* h)
 {
-    const unsigned int act = __activemask();
     const uint32_t d = digit<S>(key);
-    #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        const bool hit = (key & prefix_mask<S>()) == (t ? p_hi : p_lo);
-        const unsigned int hm = __ballot_sync(act, hit);
-        if (hit) {
-            const unsigned int peers = __match_any_sync(hm, d);
-            if ((threadIdx.x & 31) == static_cast<unsigned int>(__ffs(peers) - 1)) atomicAdd(&h[t][d], __popc(peers));
-        }
-    }
+    if ((key & prefix_mask<S>()) == p_lo) atomicAdd(h + d, 1u);
+    if ((key & prefix_mask<S>()) == p_hi) atomicAdd(h + NBIN + d, 1u);
 }
 
 // Pass S: histograms of the next digit for both targets of variate
-// blockIdx.y, merged into hist[j][t][bin].
+// blockIdx.y, merged into hist[j][t][bin].  In pass 0 every key counts for
+// both targets, so one histogram serves both (row t = 0), kept per warp in
+// shared memory to spread the atomics of keys with equal leading digits.
 template <int S>
 __global__ void __launch_bounds__(TPB)
 k_sel_hist(const float* __restrict__ proj, long long P, int vec, const DevModel* __restrict__ dm,
            unsigned int* __restrict__ hist)
 {
-    __shared__ unsigned int h[2][NBIN];
-    const int j = blockIdx.y;
-    for (int i = threadIdx.x; i < 2 * NBIN; i += TPB) (&h[0][0])[i] = 0u;
+    extern __shared__ unsigned int hs[];  // S == 0: NWARP x NBIN; else 2 x NBIN
+    constexpr int NWARP = TPB / 32;
+    constexpr int NH = S == 0 ? NWARP : 2;
+    const int j = blockIdx.y, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < NH * NBIN; i += TPB) hs[i] = 0u;
     const uint32_t p_lo = dm->sel_prefix[2 * j], p_hi = dm->sel_prefix[2 * j + 1];
     __syncthreads();
+    unsigned int* hw = hs + warp * NBIN;
     const float* src = proj + static_cast<long long>(j) * P;
     const long long stride = static_cast<long long>(gridDim.x) * TPB;
     const long long start = static_cast<long long>(blockIdx.x) * TPB + threadIdx.x;
@@ -90,19 +89,39 @@ k_sel_hist(const float* __restrict__ proj, long long P, int vec, const DevModel*
         const long long n4 = P / 4;
         for (long long g = start; g < n4; g += stride) {
             const float4 v = __ldcs(reinterpret_cast<const float4*>(src) + g);
-            count_key<S>(float_key(v.x), p_lo, p_hi, h);
-            count_key<S>(float_key(v.y), p_lo, p_hi, h);
-            count_key<S>(float_key(v.z), p_lo, p_hi, h);
-            count_key<S>(float_key(v.w), p_lo, p_hi, h);
+            if (S == 0) {
+                atomicAdd(hw + digit<0>(float_key(v.x)), 1u);
+                atomicAdd(hw + digit<0>(float_key(v.y)), 1u);
+                atomicAdd(hw + digit<0>(float_key(v.z)), 1u);
+                atomicAdd(hw + digit<0>(float_key(v.w)), 1u);
+            } else {
+                count_key<S>(float_key(v.x), p_lo, p_hi, hs);
+                count_key<S>(float_key(v.y), p_lo, p_hi, hs);
+                count_key<S>(float_key(v.z), p_lo, p_hi, hs);
+                count_key<S>(float_key(v.w), p_lo, p_hi, hs);
+            }
         }
         done = n4 * 4;
     }
-    for (long long p = done + start; p < P; p += stride) count_key<S>(float_key(src[p]), p_lo, p_hi, h);
+    for (long long p = done + start; p < P; p += stride) {
+        const uint32_t key = float_key(src[p]);
+        if (S == 0) atomicAdd(hw + digit<0>(key), 1u);
+        else count_key<S>(key, p_lo, p_hi, hs);
+    }
     __syncthreads();
     unsigned int* g = hist + static_cast<long long>(j) * 2 * NBIN;
-    for (int i = threadIdx.x; i < 2 * NBIN; i += TPB) {
-        const unsigned int c = (&h[0][0])[i];
-        if (c) atomicAdd(g + i, c);
+    if (S == 0) {
+        for (int i = threadIdx.x; i < NBIN; i += TPB) {
+            unsigned int c = 0;
+            #pragma unroll
+            for (int w = 0; w < NWARP; ++w) c += hs[w * NBIN + i];
+            if (c) atomicAdd(g + i, c);
+        }
+    } else {
+        for (int i = threadIdx.x; i < 2 * NBIN; i += TPB) {
+            const unsigned int c = hs[i];
+            if (c) atomicAdd(g + i, c);
+        }
     }
 }
 
@@ -124,10 +143,11 @@ k_sel_pick(DevModel* __restrict__ dm, unsigned int* __restrict__ hist, float* __
             s_bin = 0u;
             s_before = 0u;
         }
+        const int row = S == 0 ? 0 : t;  // pass 0 keeps one histogram for both targets
         unsigned int c[PER], sum = 0;
         #pragma unroll
         for (int i = 0; i < PER; ++i) {
-            c[i] = g[t * NBIN + tid * PER + i];
+            c[i] = g[row * NBIN + tid * PER + i];
             sum += c[i];
         }
         unsigned int v = sum;
@@ -175,14 +195,18 @@ cudaError_t launch_percentile_range(const float* proj, int k, long long P, long 
     if (gx > cap) gx = cap;
     if (gx < 1) gx = 1;
     const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(k));
-    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * 2 * NBIN * k, s);
+    const int smem0 = (TPB / 32) * NBIN * static_cast<int>(sizeof(unsigned int));
+    const int smem1 = 2 * NBIN * static_cast<int>(sizeof(unsigned int));
+    cudaError_t e = cudaFuncSetAttribute(k_sel_hist<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem0);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * 2 * NBIN * k, s);
     if (e != cudaSuccess) return e;
     k_sel_init<<<1, 2 * MAXB, 0, s>>>(dm, k, static_cast<unsigned int>(m), static_cast<unsigned int>(P));
-    k_sel_hist<0><<<grid, TPB, 0, s>>>(proj, P, vec, dm, hist);
+    k_sel_hist<0><<<grid, TPB, smem0, s>>>(proj, P, vec, dm, hist);
     k_sel_pick<0><<<k, TPB, 0, s>>>(dm, hist, range_out);
-    k_sel_hist<1><<<grid, TPB, 0, s>>>(proj, P, vec, dm, hist);
+    k_sel_hist<1><<<grid, TPB, smem1, s>>>(proj, P, vec, dm, hist);
     k_sel_pick<1><<<k, TPB, 0, s>>>(dm, hist, range_out);
-    k_sel_hist<2><<<grid, TPB, 0, s>>>(proj, P, vec, dm, hist);
+    k_sel_hist<2><<<grid, TPB, smem1, s>>>(proj, P, vec, dm, hist);
     k_sel_pick<2><<<k, TPB, 0, s>>>(dm, hist, range_out);
     return cudaGetLastError();
 }
