@@ -73,6 +73,8 @@ def _load():
         lib.orc_to_u16.argtypes = [P, I64, I64, P, P]
         lib.orc_to_u16.restype = None
         lib.orc_percentile_range.argtypes = [P, I64, I64, I64, P]
+        lib.orc_pca_cov.argtypes = [P, I64, I64, P, P, P, P]
+        lib.orc_pca_cov.restype = ctypes.c_int
         lib.orc_percentile_range.restype = ctypes.c_int
         for name in ("orc_class_sums", "orc_scatter", "orc_gen_eig", "orc_project"):
             getattr(lib, name).restype = ctypes.c_int
@@ -236,3 +238,27 @@ def percentile_range(y: np.ndarray, percent: float) -> np.ndarray:
     if rc != 0:
         raise OracleError(rc, "orc_percentile_range")
     return r
+
+
+def pca(cube: np.ndarray, mask: Optional[np.ndarray] = None) -> Dict[str, np.ndarray]:
+    """Principal components of the pixels selected by `mask` (all pixels when
+    None): Section 2's PCA -- subtract the mean, form the covariance matrix
+    (sample covariance, divided by N - 1), take its eigenvectors,
+    orthonormal.  The eigenproblem is the same solver with Sw = I, so the
+    order (descending) and the sign convention match the CVA vectors."""
+    lib = _load()
+    cube, B, P = _planar(cube)
+    mp = None
+    if mask is not None:
+        mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        if mask.size != P:
+            raise ValueError("mask must have one entry per pixel")
+        mp = _ptr(mask)
+    mu = np.zeros(B)
+    C = np.zeros((B, B))
+    N = ctypes.c_int64(0)
+    rc = lib.orc_pca_cov(_ptr(cube), B, P, mp, _ptr(mu), _ptr(C), ctypes.addressof(N))
+    if rc != OK:
+        raise OracleError(rc, "pca_cov")
+    lam, V, sweeps = gen_eig(np.eye(B), C)
+    return {"N": int(N.value), "mu": mu, "C": C, "lam": lam, "V": V, "sweeps": sweeps}

@@ -39,6 +39,11 @@
  *   - the 8-bit value is floor(255 (y - lo) / (hi - lo) + 1/2) clamped to
  *     0..255, and 0 everywhere when hi <= lo; the 16-bit value (Section 2's
  *     CVA-GSL tool writes 8- and 16-bit images) the same with 65535;
+ *   - principal components (Section 2: the unsupervised PCA of the whole
+ *     page, optionally cropped to the folio) are the eigenvectors of the
+ *     sample covariance sum_p (x_p - mu)(x_p - mu)^T / (N - 1) of the
+ *     selected pixels, orthonormal, with the same order and sign convention;
+ *     they come from the same solver with Sw = I;
  *   - the third rescale takes p percent of the pixels out of EACH tail:
  *     with m = floor(p P / 100), lo is the (m+1)-th smallest and hi the
  *     (m+1)-th largest value of the projection, p in steps of 0.01 below 50
@@ -419,5 +424,37 @@ int orc_percentile_range(const double* y, int64_t k, int64_t P, int64_t bp, doub
         range[2 * j + 1] = v[P - 1 - m];
     }
     free(v);
+    return ORC_OK;
+}
+
+
+/* Mean and sample covariance of the pixels selected by mask (all pixels when
+ * mask is NULL), in two passes: mu = sum x_p / N, then
+ * C = sum (x_p - mu)(x_p - mu)^T / (N - 1).  *N_out = N. */
+int orc_pca_cov(const uint16_t* cube, int64_t B, int64_t P, const uint8_t* mask, double* mu, double* C,
+                int64_t* N_out)
+{
+    if (B < 1 || P < 1) return ORC_ERR_ARG;
+    int64_t N = 0;
+    for (int64_t b = 0; b < B; ++b) mu[b] = 0.0;
+    for (int64_t p = 0; p < P; ++p) {
+        if (mask && mask[p] == 0) continue;
+        ++N;
+        for (int64_t b = 0; b < B; ++b) mu[b] += (double)cube[b * P + p];
+    }
+    *N_out = N;
+    if (N < 2) return ORC_ERR_EMPTY_CLASS;
+    for (int64_t b = 0; b < B; ++b) mu[b] /= (double)N;
+    for (int64_t i = 0; i < B * B; ++i) C[i] = 0.0;
+    double* d = (double*)malloc(sizeof(double) * (size_t)B);
+    if (!d) return ORC_ERR_ARG;
+    for (int64_t p = 0; p < P; ++p) {
+        if (mask && mask[p] == 0) continue;
+        for (int64_t b = 0; b < B; ++b) d[b] = (double)cube[b * P + p] - mu[b];
+        for (int64_t i = 0; i < B; ++i)
+            for (int64_t j = 0; j < B; ++j) C[i * B + j] += d[i] * d[j];
+    }
+    free(d);
+    for (int64_t i = 0; i < B * B; ++i) C[i] /= (double)(N - 1);
     return ORC_OK;
 }

@@ -377,6 +377,75 @@ def test_percentile_range_special_cases():
 
 
 # --------------------------------------------------------------------------
+# principal components (Section 2: unsupervised PCA of the page)
+# --------------------------------------------------------------------------
+
+def _pca_cube(seed=31, B=6, H=20, W=30):
+    w = make_workload(seed, B, H, W, 3, (60, 60, 60), 2, separation=(1.0, 3.0))
+    return w
+
+
+def test_pca_matches_numpy_cov_and_eigh():
+    w = _pca_cube()
+    X = w.cube.reshape(w.B, -1).astype(np.float64)
+    r = oracle.pca(w.cube)
+    np.testing.assert_allclose(r["mu"], X.mean(axis=1), rtol=1e-13)
+    np.testing.assert_allclose(r["C"], np.cov(X), rtol=1e-11, atol=1e-9 * np.abs(np.cov(X)).max())
+    lam, U = np.linalg.eigh(np.cov(X))
+    lam, U = lam[::-1], U[:, ::-1]
+    np.testing.assert_allclose(r["lam"], lam, rtol=1e-10, atol=1e-10 * lam[0])
+    for j in range(w.B):  # distinct eigenvalues: vectors equal up to sign
+        assert abs(abs(r["V"][:, j] @ U[:, j]) - 1.0) <= 1e-9
+
+
+def test_pca_invariants():
+    w = _pca_cube(seed=32, B=9)
+    r = oracle.pca(w.cube)
+    V, lam, C = r["V"], r["lam"], r["C"]
+    np.testing.assert_allclose(V.T @ V, np.eye(w.B), atol=1e-12)
+    np.testing.assert_allclose(C @ V, V * lam, atol=1e-10 * lam[0])
+    assert abs(lam.sum() - np.trace(C)) <= 1e-12 * np.trace(C)  # total variance
+    assert np.all(np.diff(lam) <= 0)
+    for j in range(w.B):  # sign convention: largest-magnitude component positive
+        v = V[:, j]
+        assert v[np.argmax(np.abs(v))] > 0
+
+
+def test_pca_mask_selects_pixels():
+    w = _pca_cube(seed=33)
+    mask = (np.arange(w.P) % 3 == 0).astype(np.uint8).reshape(w.H, w.W)
+    r = oracle.pca(w.cube, mask)
+    sub = w.cube.reshape(w.B, -1)[:, mask.reshape(-1) > 0]
+    r2 = oracle.pca(sub.reshape(w.B, 1, -1))
+    assert r["N"] == sub.shape[1]
+    np.testing.assert_array_equal(r["mu"], r2["mu"])
+    np.testing.assert_array_equal(r["C"], r2["C"])
+
+
+def test_pca_band_permutation():
+    w = _pca_cube(seed=34, B=7)
+    perm = np.array([3, 0, 6, 1, 5, 2, 4])
+    r = oracle.pca(w.cube)
+    rp = oracle.pca(w.cube[perm])
+    np.testing.assert_allclose(rp["lam"], r["lam"], rtol=1e-11)
+    np.testing.assert_allclose(rp["V"], r["V"][perm], atol=1e-9)
+
+
+def test_pca_rank_one_closed_form():
+    """Pixels on a line x = a + t d: one component, lambda = var(t) |d|^2."""
+    rng = np.random.default_rng(35)
+    t = rng.integers(0, 40, size=500)
+    d = np.array([3, -1, 2, 5])
+    a = np.array([1000, 2000, 1500, 500])
+    cube = (a[:, None] + t[None, :] * d[:, None]).astype(np.uint16).reshape(4, 20, 25)
+    r = oracle.pca(cube)
+    lam1 = np.var(t, ddof=1) * float(d @ d)
+    assert abs(r["lam"][0] - lam1) <= 1e-11 * lam1
+    np.testing.assert_allclose(r["V"][:, 0], d / np.linalg.norm(d), atol=1e-12)
+    assert np.all(np.abs(r["lam"][1:]) <= 1e-9 * lam1)
+
+
+# --------------------------------------------------------------------------
 # errors
 # --------------------------------------------------------------------------
 
