@@ -318,6 +318,15 @@ def _other_outputs(cva, torch, w, m, cube, stream, peak):
                                                                      stream=stream), stream), 6 * k * P)
     t = res["project_f32"]["ms"] + res["percentile_range_1pct"]["ms"] + res["to_u8_given"]["ms"]
     res["third_rescale_u8_image_mpixel_s"] = P / (t * 1e-3) / 1e6
+    # principal components of the whole page (exact moments of every pixel
+    # on the tensor cores, then the 23 x 23 eigensolve), on a model of its own
+    mp = cva.Model(w.B, 2)
+    cva.cva_set_variates(mp, k)
+    entry("pca_fit_whole_page", _time_calls(torch, lambda: cva.cva_pca_fit(cube, mp, stream=stream), stream),
+          P * 2 * w.B)
+    F = (w.B + 1 + 7) // 8 * 8
+    res["pca_fit_whole_page"]["mma_tflops"] = P * (2 * F) ** 2 * 2 / (res["pca_fit_whole_page"]["ms"] * 1e-3) / 1e12
+    mp.close()
     return res
 
 

@@ -131,6 +131,27 @@ int cva_set_variates(cva_model* m, int nvec);
 int cva_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, int K,
             cva_model* m, void* stream);
 
+/* Principal components instead of canonical variates (Section 2: the
+ * unsupervised PCA of the whole page -- subtract the mean, form the
+ * covariance matrix, take its eigenvectors, orthonormal -- and, with a mask,
+ * of the folio cropped out of the page or of chosen points).  The model's
+ * eigenvalues become those of the sample covariance
+ * C = sum_p (x_p - mu)(x_p - mu)^T / (N - 1) over the N selected pixels, in
+ * descending order, and V its orthonormal eigenvectors (V^T V = I, same sign
+ * convention), mean the mean of the selected pixels.  The moments are exact
+ * (64-bit integer sums from BF16 hi/lo split values on the tensor cores),
+ * the eigensolve as for cva_fit.  Afterwards cva_project, cva_project_u8 and
+ * cva_to_u8 / cva_to_u16 work with CVA_RANGE_GLOBAL and CVA_RANGE_GIVEN
+ * (there are no training pixels: CVA_RANGE_TRAINING is refused), and
+ * cva_model_get_scatter returns counts[0] = N, class_means[0] = mean,
+ * Sw = C and Sb = 0.  The model's K is not used.
+ *   cube   device, B x H x W uint16 (B = the model's band count)
+ *   mask   device, H x W uint8 (nonzero = pixel used), or NULL for all
+ * Device errors: CVA_ERR_EMPTY_CLASS when fewer than 2 pixels are selected.
+ * Asynchronous; allocates nothing. */
+int cva_pca_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* mask, cva_model* m,
+                void* stream);
+
 /* Synchronize `stream` and return the model's device status (CVA_OK or the
  * first device-side error of the last fit). */
 int cva_status(cva_model* m, void* stream);

@@ -53,6 +53,7 @@ SIGNATURES = {
     "cva_project": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P]),
     "cva_to_u8": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "cva_project_u8": (_I, [_P, _I, _I, _I, _P, _I, _I, _P, _P, _P]),
+    "cva_pca_fit": (_I, [_P, _I, _I, _I, _P, _P, _P]),
     "cva_percentile_range": (_I, [_P, _I, _I, _I, ctypes.c_double, _P, _P, _P]),
     "cva_to_u16": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "cva_fit_project_u8_noalloc": (_I, [_P, _I, _I, _I, _P, _I, _I, _P, _P, _P, _P]),
@@ -353,3 +354,12 @@ def cva_to_u16(proj: torch.Tensor, mode: int, out: torch.Tensor, m: Optional[Mod
     _check(load().cva_to_u16(_dptr(proj, torch.float32, "proj"), k, H, W, mode,
                              _dptr(range, torch.float32, "range"), m.handle if m is not None else None,
                              _dptr(out, torch.uint16, "out"), _stream_ptr(stream)), "cva_to_u16")
+
+
+def cva_pca_fit(cube: torch.Tensor, m: Model, mask: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Principal components of the page (or of the masked pixels) into ``m``."""
+    B, H, W = cube.shape
+    if mask is not None and tuple(mask.shape) != (H, W):
+        raise ValueError("mask must be H x W")
+    _check(load().cva_pca_fit(_dptr(cube, torch.uint16, "cube"), B, H, W, _dptr(mask, torch.uint8, "mask"),
+                              m.handle, _stream_ptr(stream)), "cva_pca_fit")

@@ -18,6 +18,7 @@ struct cva_model {
     int precision;
     int fit_nvec;        // canonical vectors formed by the last fit
     bool range64_valid;  // dm->train_enc64 belongs to the last fit
+    bool pca;            // the last fit was a principal-component fit (no training range)
     cva::DevModel* dm;
     unsigned int* tiles; // per-tile class counts, then first rows (MAX_TILES x (K + 1))
     unsigned int* list;  // class-major training-pixel indices, cap entries
@@ -146,6 +147,7 @@ int cva_model_create(int B, int K, cva_model** out)
     m->precision = CVA_PRECISION_MIXED;
     m->fit_nvec = B;
     m->range64_valid = false;
+    m->pca = false;
     m->dm = dm;
     m->tiles = tiles;
     m->list = list;
@@ -216,7 +218,23 @@ int cva_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, in
     if (e == cudaSuccess) e = cva::launch_train_range(B, K, m->xtr, m->dm, m->nvec, m->num_sms, s);
     m->fit_nvec = m->nvec;
     m->range64_valid = false;
+    m->pca = false;
     if (e == cudaSuccess && m->precision == CVA_PRECISION_FP64) e = ensure_range64(m, s);
+    return from_cuda(e);
+}
+
+int cva_pca_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* mask, cva_model* m, void* stream)
+{
+    if (!m || B != m->B || !valid_dims(B, H, W)) return CVA_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(cube) % 2 != 0) return CVA_ERR_INVALID_ARG;
+    if (!device_visible(cube) || (mask && !device_visible(mask))) return CVA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long P = static_cast<long long>(H) * W;
+    cudaError_t e = cva::launch_pca_moments(cube, B, P, mask, m->dm, m->num_sms, s);
+    if (e == cudaSuccess) e = cva::launch_pca_finalize(m->dm, B, m->nvec, s);
+    m->fit_nvec = m->nvec;
+    m->range64_valid = false;
+    m->pca = true;
     return from_cuda(e);
 }
 
@@ -239,7 +257,7 @@ int cva_model_get(cva_model* m, double* eigvals, double* V, double* mean, float*
         return CVA_ERR_CUDA;
     if (mean && cudaMemcpy(mean, dm->mu, sizeof(double) * B, cudaMemcpyDeviceToHost) != cudaSuccess)
         return CVA_ERR_CUDA;
-    if (train_range && m->precision == CVA_PRECISION_FP64) {
+    if (train_range && m->precision == CVA_PRECISION_FP64 && !m->pca) {
         unsigned long long enc[2 * cva::MAXB];
         if (ensure_range64(m, static_cast<cudaStream_t>(stream)) != cudaSuccess ||
             cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess ||
@@ -334,7 +352,7 @@ int cva_to_u8(const float* proj, int k, int H, int W, int mode, const float* ran
             if (e == cudaSuccess) e = cva::launch_f32_to_u8(proj, k, P, dmc, m->dm->work_range, out, m->num_sms, s);
             break;
         case CVA_RANGE_TRAINING:
-            if (!m || k > m->fit_nvec) return CVA_ERR_INVALID_ARG;
+            if (!m || k > m->fit_nvec || m->pca) return CVA_ERR_INVALID_ARG;
             e = cva::launch_f32_to_u8(proj, k, P, dmc, m->dm->train_range, out, m->num_sms, s);
             break;
         case CVA_RANGE_GIVEN: {
@@ -396,7 +414,7 @@ int cva_to_u16(const float* proj, int k, int H, int W, int mode, const float* ra
             if (e == cudaSuccess) e = cva::launch_f32_to_u16(proj, k, P, m->dm->work_range, out, sms, s);
             break;
         case CVA_RANGE_TRAINING:
-            if (!m || k > m->fit_nvec) return CVA_ERR_INVALID_ARG;
+            if (!m || k > m->fit_nvec || m->pca) return CVA_ERR_INVALID_ARG;
             e = cva::launch_f32_to_u16(proj, k, P, m->dm->train_range, out, sms, s);
             break;
         case CVA_RANGE_GIVEN:
@@ -420,6 +438,7 @@ int cva_project_u8(const uint16_t* cube, int B, int H, int W, cva_model* m, int 
     const long long P = static_cast<long long>(H) * W;
     DevModel* dm = m->dm;
     cudaError_t e = cudaSuccess;
+    if (mode == CVA_RANGE_TRAINING && m->pca) return CVA_ERR_INVALID_ARG;
     if (m->precision == CVA_PRECISION_FP64) {
         switch (mode) {
             case CVA_RANGE_TRAINING:

@@ -132,6 +132,12 @@ cudaError_t launch_f32_range(const float* proj, int k, long long P, const DevMod
 cudaError_t launch_f32_to_u8(const float* proj, int k, long long P, const DevModel* dm,
                              const float* range, uint8_t* out, int num_sms, cudaStream_t s);
 
+// Principal components of the pixels selected by `mask` (all when null):
+// exact moments into class 0 of the model, then the B x B eigensolve.
+cudaError_t launch_pca_moments(const uint16_t* cube, int B, long long P, const uint8_t* mask, DevModel* dm,
+                               int num_sms, cudaStream_t s);
+cudaError_t launch_pca_finalize(DevModel* dm, int B, int nvec, cudaStream_t s);
+
 // Third rescale: lo / hi of each of k projections with m values taken out of
 // each tail (`hist`: 2 x 2048 words per variate, zero on entry and on exit).
 cudaError_t launch_percentile_range(const float* proj, int k, long long P, long long m, DevModel* dm,

@@ -51,24 +51,34 @@ constexpr int JACOBI_SWEEPS = 40;
 constexpr int REFINE_STEPS = 3;
 constexpr int MAXTRI = MAXB * (MAXB + 1) / 2;
 
+// Work space of the symmetric eigensolver for matrices of order <= NM.
+template <int NM>
+struct SymEig {
+    df T[NM][NM + 1];       // the matrix, about unit norm
+    df W[NM][NM + 1];       // eigenvectors (columns), refined
+    df R[NM][NM + 1];
+    df TW[NM][NM + 1];
+    df S[NM][NM + 1];
+    df E[NM][NM + 1];
+    float Tf[NM][NM + 1];   // FP32 copy of T, diagonalized in place
+    float Wf[NM][NM + 1];   // FP32 eigenvectors (identity on entry)
+    df lam[NM];             // eigenvalues, in W's column order
+    float rc[NM / 2], rs[NM / 2];
+    int rp[NM / 2], rq[NM / 2], rok[NM / 2];
+    unsigned char rr[NM][NM];
+    float red[3][NWARP];
+};
+
 struct FinSmem {
     df A[MAXB][2 * MAXB + MAXK + 1];  // [Sw | Mb | I] during elimination
     df L[MAXB][MAXB + 1];
     df G[MAXB][MAXK + 1];
     df Li[MAXB][MAXB + 1];        // L^-1 (lower triangular)
-    df T[MAXK][MAXK + 1];
-    df W[MAXK][MAXK + 1];
-    df R[MAXK][MAXK + 1];
-    df TW[MAXK][MAXK + 1];
-    df S[MAXK][MAXK + 1];
-    df E[MAXK][MAXK + 1];
-    float Tf[MAXK][MAXK + 1];
-    float Wf[MAXK][MAXK + 1];
+    SymEig<MAXK> eig;             // T = G^T G and its eigen-decomposition
     df U[MAXB][MAXB + 1];
     df V[MAXB][MAXB + 1];
     df mu[MAXB];
     df invd[MAXB];
-    df lamk[MAXK];
     df lam[MAXB];
     df q[MAXB];
     df cvec[MAXB];
@@ -76,10 +86,7 @@ struct FinSmem {
     df sqn[MAXK];
     float swd[MAXB];
     float res[MAXB];
-    float rc[MAXK / 2], rs[MAXK / 2];
-    int rp[MAXK / 2], rq[MAXK / 2], rok[MAXK / 2];
     int order[MAXK];
-    unsigned char rr[MAXK][MAXK];
     unsigned long long n[MAXK];
     unsigned long long tot[MAXB];
     unsigned char tri_i[MAXTRI], tri_l[MAXTRI];
@@ -120,6 +127,171 @@ __device__ inline df warp_sum_df(df v)
 __device__ inline int rr_player(int i, int round, int n)
 {
     return i == 0 ? 0 : 1 + (i - 1 + round) % (n - 1);
+}
+
+// Block-wide maximum of a per-thread float (slot selects the scratch row).
+template <int NM>
+__device__ inline float block_maxf(SymEig<NM>& e, float v, int slot)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    if (lane == 0) e.red[slot][warp] = v;
+    __syncthreads();
+    float m = e.red[slot][0];
+    for (int w = 1; w < NWARP; ++w) m = fmaxf(m, e.red[slot][w]);
+    return m;
+}
+
+// Eigen-decomposition of the symmetric n x n matrix e.T (n <= NM, scaled to
+// about unit norm; e.Tf holds its FP32 copy and e.Wf the identity on entry).
+// The cyclic Jacobi method in FP32 (round-robin order) runs on warp 0; the
+// eigenvectors are then refined in double-float by the Ogita-Aishima
+// iteration for symmetric eigendecompositions (T. Ogita, K. Aishima,
+// "Iterative refinement for symmetric eigenvalue decomposition", Japan J.
+// Indust. Appl. Math. 35, 2018), whose matrix products are spread over the
+// whole block.  Leaves the eigenvectors in e.W (columns) and the eigenvalues
+// in e.lam, unsorted.  Every thread of the block calls it.
+template <int NM>
+__device__ void sym_eig(SymEig<NM>& e, int n)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (warp == 0) {
+        const int m = n + (n & 1), half = m / 2;
+        for (int q = lane; q < (m - 1) * m; q += 32) {  // round-robin seating, one row per round
+            const int round = q / m, seat = q - (q / m) * m;
+            e.rr[round][seat] = static_cast<unsigned char>(rr_player(seat, round, m));
+        }
+        float tot = 0.0f;
+        for (int q = lane; q < n * n; q += 32) tot = fmaf(e.Tf[q / n][q % n], e.Tf[q / n][q % n], tot);
+        tot = warp_sumf(tot);
+        __syncwarp();
+        float prev = 3.0e38f;
+        for (int sweep = 0; sweep < JACOBI_SWEEPS; ++sweep) {
+            float off = 0.0f;
+            for (int q = lane; q < n * n; q += 32) {
+                const int a = q / n, b = q % n;
+                if (a != b) off = fmaf(e.Tf[a][b], e.Tf[a][b], off);
+            }
+            off = warp_sumf(off);
+            if (off <= 1e-11f * tot || off >= 0.25f * prev) break;  // converged, or stalled at FP32 rounding
+            prev = off;
+            for (int round = 0; round < m - 1; ++round) {
+                if (lane < half) {
+                    const int a = e.rr[round][lane], b = e.rr[round][m - 1 - lane];
+                    const int p = min(a, b), q = max(a, b);
+                    int ok = 0;
+                    float cs = 1.0f, sn = 0.0f;
+                    if (q < n) {
+                        const float apq = e.Tf[p][q];
+                        if (apq != 0.0f) {
+                            // approximate intrinsics suffice: the refinement below
+                            // restores accuracy, only orthogonal-enough rotations matter
+                            const float tau = __fdividef(e.Tf[q][q] - e.Tf[p][p], 2.0f * apq);
+                            float t;
+                            if (fabsf(tau) > 1e15f) t = __fdividef(0.5f, tau);
+                            else t = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.0f))), tau);
+                            cs = rsqrtf(fmaf(t, t, 1.0f));
+                            sn = t * cs;
+                            ok = 1;
+                        }
+                    }
+                    e.rp[lane] = p;
+                    e.rq[lane] = q;
+                    e.rc[lane] = cs;
+                    e.rs[lane] = sn;
+                    e.rok[lane] = ok;
+                }
+                __syncwarp();
+                for (int q = lane; q < n * half; q += 32) {  // T <- T J
+                    const int r = q % n, w = q / n;
+                    if (!e.rok[w]) continue;
+                    const int p = e.rp[w], qq = e.rq[w];
+                    const float cs = e.rc[w], sn = e.rs[w];
+                    const float a = e.Tf[r][p], b = e.Tf[r][qq];
+                    e.Tf[r][p] = cs * a - sn * b;
+                    e.Tf[r][qq] = sn * a + cs * b;
+                }
+                __syncwarp();
+                for (int q = lane; q < n * half; q += 32) {  // T <- J^T T, W <- W J
+                    const int r = q % n, w = q / n;
+                    if (!e.rok[w]) continue;
+                    const int p = e.rp[w], qq = e.rq[w];
+                    const float cs = e.rc[w], sn = e.rs[w];
+                    const float a = e.Tf[p][r], b = e.Tf[qq][r];
+                    e.Tf[p][r] = cs * a - sn * b;
+                    e.Tf[qq][r] = sn * a + cs * b;
+                    const float wa = e.Wf[r][p], wb = e.Wf[r][qq];
+                    e.Wf[r][p] = cs * wa - sn * wb;
+                    e.Wf[r][qq] = sn * wa + cs * wb;
+                }
+                __syncwarp();
+            }
+        }
+    }
+    __syncthreads();
+
+    // Ogita-Aishima refinement of the eigenvectors W of T in double-float
+    const int nn = n * n;
+    for (int q = tid; q < nn; q += TPB) e.W[q / n][q % n] = df_from(e.Wf[q / n][q % n]);
+    __syncthreads();
+    for (int it = 0; it < REFINE_STEPS; ++it) {
+        for (int q = tid; q < nn; q += TPB) {
+            const int a = q / n, b = q % n;
+            df r = df_from(0.0f), tw = df_from(0.0f);
+            for (int k = 0; k < n; ++k) {
+                r = df_fma(r, e.W[k][a], e.W[k][b]);     // W^T W
+                tw = df_fma(tw, e.T[a][k], e.W[k][b]);   // T W
+            }
+            e.R[a][b] = df_sub(df_from(a == b ? 1.0f : 0.0f), r);  // I - W^T W
+            e.TW[a][b] = tw;
+        }
+        __syncthreads();
+        float so = 0.0f, lm = 0.0f, rm = 0.0f;
+        for (int q = tid; q < nn; q += TPB) {
+            const int a = q / n, b = q % n;
+            df sv = df_from(0.0f);
+            for (int k = 0; k < n; ++k) sv = df_fma(sv, e.W[k][a], e.TW[k][b]);  // W^T T W
+            e.S[a][b] = sv;
+            if (a != b) so = fmaxf(so, fabsf(sv.hi));
+            else lm = fmaxf(lm, fabsf(sv.hi));
+            rm = fmaxf(rm, fabsf(e.R[a][b].hi));
+        }
+        so = block_maxf(e, so, 0);
+        lm = block_maxf(e, lm, 1);
+        rm = block_maxf(e, rm, 2);
+        const float delta = 2.0f * (so + lm * rm);  // cluster threshold
+        if (tid < n) {  // lambda_i = s_ii / (1 - r_ii) = s_ii (1 + r_ii + r_ii^2 + ...)
+            const df r = e.R[tid][tid];
+            e.lam[tid] = df_mul(e.S[tid][tid], df_add(df_from(1.0f), df_mul(r, df_add(df_from(1.0f), r))));
+        }
+        __syncthreads();
+        float emax = 0.0f;
+        for (int q = tid; q < nn; q += TPB) {
+            const int a = q / n, b = q % n;
+            df ev;
+            const df gap = df_sub(e.lam[b], e.lam[a]);
+            if (a == b || fabsf(gap.hi) <= delta) {
+                ev = df_mulf(e.R[a][b], 0.5f);
+            } else {
+                const df num = df_fma(e.S[a][b], e.lam[b], e.R[a][b]);
+                ev = df_from(num.hi / gap.hi);
+            }
+            e.E[a][b] = ev;
+            emax = fmaxf(emax, fabsf(ev.hi));
+        }
+        __syncthreads();  // E complete; the red rows are free again
+        emax = block_maxf(e, emax, 0);
+        for (int q = tid; q < nn; q += TPB) {
+            const int a = q / n, b = q % n;
+            df d = df_from(0.0f);
+            for (int k = 0; k < n; ++k) d = df_fma(d, e.W[a][k], e.E[k][b]);  // W E
+            e.TW[a][b] = d;
+        }
+        __syncthreads();
+        for (int q = tid; q < nn; q += TPB) e.W[q / n][q % n] = df_add(e.W[q / n][q % n], e.TW[q / n][q % n]);
+        __syncthreads();
+        if (emax < 1e-6f) break;  // the next correction would be below the double-float rounding
+    }
 }
 
 // Complete U[:, j0 .. j1) to an orthonormal set with pivoted Gram-Schmidt:
@@ -331,12 +503,12 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
             for (int i = sub; i < B; i += per) s = df_fma(s, sm.G[i][a], sm.G[i][b]);
         }
         for (int o = per / 2; o > 0; o >>= 1) s = df_add(s, shfl_xor_df(s, o));
-        if (e < KK && sub == 0) sm.T[e / K][e % K] = s;
+        if (e < KK && sub == 0) sm.eig.T[e / K][e % K] = s;
     }
     __syncthreads();
     if (tid < 32) {
         float f = 0.0f;
-        for (int e = tid; e < K * K; e += 32) f = fmaf(sm.T[e / K][e % K].hi, sm.T[e / K][e % K].hi, f);
+        for (int e = tid; e < K * K; e += 32) f = fmaf(sm.eig.T[e / K][e % K].hi, sm.eig.T[e / K][e % K].hi, f);
         f = warp_sumf(f);
         if (tid == 0) {
             int ex = 0;
@@ -348,152 +520,14 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
     const float scale = sm.scale;
     if (tid < K * K) {
         const int a = tid / K, b = tid % K;
-        sm.T[a][b] = df_mulf(sm.T[a][b], scale);  // exact: a power of two
-        sm.Tf[a][b] = sm.T[a][b].hi;
-        sm.Wf[a][b] = (a == b) ? 1.0f : 0.0f;
+        sm.eig.T[a][b] = df_mulf(sm.eig.T[a][b], scale);  // exact: a power of two
+        sm.eig.Tf[a][b] = sm.eig.T[a][b].hi;
+        sm.eig.Wf[a][b] = (a == b) ? 1.0f : 0.0f;
     }
     __syncthreads();
 
-    // ---- 4. FP32 cyclic Jacobi on T, then 5. refinement (one warp) ----------
-    if (warp == 0) {
-        const int n = K + (K & 1), half = n / 2;
-        for (int e = lane; e < (n - 1) * n; e += 32) {  // round-robin seating, one row per round
-            const int round = e / n, seat = e - (e / n) * n;
-            sm.rr[round][seat] = static_cast<unsigned char>(rr_player(seat, round, n));
-        }
-        float tot = 0.0f;
-        for (int e = lane; e < K * K; e += 32) tot = fmaf(sm.Tf[e / K][e % K], sm.Tf[e / K][e % K], tot);
-        tot = warp_sumf(tot);
-        __syncwarp();
-        float prev = 3.0e38f;
-        for (int sweep = 0; sweep < JACOBI_SWEEPS; ++sweep) {
-            float off = 0.0f;
-            for (int e = lane; e < K * K; e += 32) {
-                const int a = e / K, b = e % K;
-                if (a != b) off = fmaf(sm.Tf[a][b], sm.Tf[a][b], off);
-            }
-            off = warp_sumf(off);
-            if (off <= 1e-11f * tot || off >= 0.25f * prev) break;  // converged, or stalled at FP32 rounding
-            prev = off;
-            for (int round = 0; round < n - 1; ++round) {
-                if (lane < half) {
-                    const int a = sm.rr[round][lane], b = sm.rr[round][n - 1 - lane];
-                    const int p = min(a, b), q = max(a, b);
-                    int ok = 0;
-                    float cs = 1.0f, sn = 0.0f;
-                    if (q < K) {
-                        const float apq = sm.Tf[p][q];
-                        if (apq != 0.0f) {
-                            // approximate intrinsics suffice: the refinement below
-                            // restores accuracy, only orthogonal-enough rotations matter
-                            const float tau = __fdividef(sm.Tf[q][q] - sm.Tf[p][p], 2.0f * apq);
-                            float t;
-                            if (fabsf(tau) > 1e15f) t = __fdividef(0.5f, tau);
-                            else t = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.0f))), tau);
-                            cs = rsqrtf(fmaf(t, t, 1.0f));
-                            sn = t * cs;
-                            ok = 1;
-                        }
-                    }
-                    sm.rp[lane] = p;
-                    sm.rq[lane] = q;
-                    sm.rc[lane] = cs;
-                    sm.rs[lane] = sn;
-                    sm.rok[lane] = ok;
-                }
-                __syncwarp();
-                for (int e = lane; e < K * half; e += 32) {  // T <- T J
-                    const int r = e % K, w = e / K;
-                    if (!sm.rok[w]) continue;
-                    const int p = sm.rp[w], q = sm.rq[w];
-                    const float cs = sm.rc[w], sn = sm.rs[w];
-                    const float a = sm.Tf[r][p], b = sm.Tf[r][q];
-                    sm.Tf[r][p] = cs * a - sn * b;
-                    sm.Tf[r][q] = sn * a + cs * b;
-                }
-                __syncwarp();
-                for (int e = lane; e < K * half; e += 32) {  // T <- J^T T, W <- W J
-                    const int r = e % K, w = e / K;
-                    if (!sm.rok[w]) continue;
-                    const int p = sm.rp[w], q = sm.rq[w];
-                    const float cs = sm.rc[w], sn = sm.rs[w];
-                    const float a = sm.Tf[p][r], b = sm.Tf[q][r];
-                    sm.Tf[p][r] = cs * a - sn * b;
-                    sm.Tf[q][r] = sn * a + cs * b;
-                    const float wa = sm.Wf[r][p], wb = sm.Wf[r][q];
-                    sm.Wf[r][p] = cs * wa - sn * wb;
-                    sm.Wf[r][q] = sn * wa + cs * wb;
-                }
-                __syncwarp();
-            }
-        }
-
-        // Ogita-Aishima refinement of the eigenvectors W of T in double-float
-        for (int e = lane; e < K * K; e += 32) sm.W[e / K][e % K] = df_from(sm.Wf[e / K][e % K]);
-        __syncwarp();
-        for (int it = 0; it < REFINE_STEPS; ++it) {
-            float emax = 0.0f;
-            for (int e = lane; e < K * K; e += 32) {
-                const int a = e / K, b = e % K;
-                df r = df_from(0.0f), tw = df_from(0.0f);
-                for (int k = 0; k < K; ++k) {
-                    r = df_fma(r, sm.W[k][a], sm.W[k][b]);     // W^T W
-                    tw = df_fma(tw, sm.T[a][k], sm.W[k][b]);   // T W
-                }
-                sm.R[a][b] = df_sub(df_from(a == b ? 1.0f : 0.0f), r);  // I - W^T W
-                sm.TW[a][b] = tw;
-            }
-            __syncwarp();
-            float so = 0.0f, lm = 0.0f, rm = 0.0f;
-            for (int e = lane; e < K * K; e += 32) {
-                const int a = e / K, b = e % K;
-                df sv = df_from(0.0f);
-                for (int k = 0; k < K; ++k) sv = df_fma(sv, sm.W[k][a], sm.TW[k][b]);  // W^T T W
-                sm.S[a][b] = sv;
-                if (a != b) so = fmaxf(so, fabsf(sv.hi));
-                else lm = fmaxf(lm, fabsf(sv.hi));
-                rm = fmaxf(rm, fabsf(sm.R[a][b].hi));
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                so = fmaxf(so, __shfl_xor_sync(0xFFFFFFFFu, so, o));
-                lm = fmaxf(lm, __shfl_xor_sync(0xFFFFFFFFu, lm, o));
-                rm = fmaxf(rm, __shfl_xor_sync(0xFFFFFFFFu, rm, o));
-            }
-            const float delta = 2.0f * (so + lm * rm);  // cluster threshold
-            __syncwarp();
-            if (lane < K) {  // lambda_i = s_ii / (1 - r_ii) = s_ii (1 + r_ii + r_ii^2 + ...)
-                const df r = sm.R[lane][lane];
-                sm.lamk[lane] = df_mul(sm.S[lane][lane], df_add(df_from(1.0f), df_mul(r, df_add(df_from(1.0f), r))));
-            }
-            __syncwarp();
-            for (int e = lane; e < K * K; e += 32) {
-                const int a = e / K, b = e % K;
-                df ev;
-                const df gap = df_sub(sm.lamk[b], sm.lamk[a]);
-                if (a == b || fabsf(gap.hi) <= delta) {
-                    ev = df_mulf(sm.R[a][b], 0.5f);
-                } else {
-                    const df num = df_fma(sm.S[a][b], sm.lamk[b], sm.R[a][b]);
-                    ev = df_from(num.hi / gap.hi);
-                }
-                sm.E[a][b] = ev;
-                emax = fmaxf(emax, fabsf(ev.hi));
-            }
-            for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, o));
-            __syncwarp();
-            for (int e = lane; e < K * K; e += 32) {
-                const int a = e / K, b = e % K;
-                df d = df_from(0.0f);
-                for (int k = 0; k < K; ++k) d = df_fma(d, sm.W[a][k], sm.E[k][b]);  // W E
-                sm.TW[a][b] = d;
-            }
-            __syncwarp();
-            for (int e = lane; e < K * K; e += 32) sm.W[e / K][e % K] = df_add(sm.W[e / K][e % K], sm.TW[e / K][e % K]);
-            __syncwarp();
-            if (emax < 1e-6f) break;  // the next correction would be below the double-float rounding
-        }
-    }
-    __syncthreads();
+    // ---- 4. FP32 cyclic Jacobi on T, then 5. refinement ----------------------
+    sym_eig<MAXK>(sm.eig, K);
 
     // ---- 6. eigenvalues in descending order, whitened eigenvectors ----------
     if (tid == 0) {
@@ -502,21 +536,21 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
             int best = -1;
             for (int i = 0; i < K; ++i) {
                 if (used & (1 << i)) continue;
-                if (best < 0 || df_gt(sm.lamk[i], sm.lamk[best])) best = i;
+                if (best < 0 || df_gt(sm.eig.lam[i], sm.eig.lam[best])) best = i;
             }
             used |= 1 << best;
             sm.order[j] = best;
         }
         const int rmax = min(K - 1, B);
-        const float top = sm.lamk[sm.order[0]].hi;
+        const float top = sm.eig.lam[sm.order[0]].hi;
         int r = 0;
-        while (r < rmax && top > 0.0f && sm.lamk[sm.order[r]].hi > 1e-12f * top) ++r;
+        while (r < rmax && top > 0.0f && sm.eig.lam[sm.order[r]].hi > 1e-12f * top) ++r;
         sm.r_eff = r;
     }
     __syncthreads();
     const int r = sm.r_eff;
     const float unscale = __frcp_rn(scale);  // a power of two: exact
-    if (tid < B) sm.lam[tid] = (tid < r) ? df_mulf(sm.lamk[sm.order[tid]], unscale) : df_from(0.0f);
+    if (tid < B) sm.lam[tid] = (tid < r) ? df_mulf(sm.eig.lam[sm.order[tid]], unscale) : df_from(0.0f);
     const int nv = nvec > B ? B : nvec;
     const int rr = r < nv ? r : nv;
     __syncthreads();
@@ -524,7 +558,7 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
         const int b = e / rr, j = e - (e / rr) * rr;
         const int w = sm.order[j];
         df s = df_from(0.0f);
-        for (int c = 0; c < K; ++c) s = df_fma(s, sm.G[b][c], sm.W[c][w]);
+        for (int c = 0; c < K; ++c) s = df_fma(s, sm.G[b][c], sm.eig.W[c][w]);
         sm.U[b][j] = df_mul(s, df_rsqrt(sm.lam[j]));
     }
     __syncthreads();
@@ -617,6 +651,150 @@ __global__ void __launch_bounds__(TPB) kb_fit_finalize(const PageDev* __restrict
     if (pg.eigvals && threadIdx.x < pg.B && pg.dm->status == 0) pg.eigvals[threadIdx.x] = pg.dm->lam[threadIdx.x];
 }
 
+// ---------------------------------------------------------------------------
+// Principal components (Section 2: subtract the mean, form the covariance
+// matrix, take its eigenvectors, orthonormal).  From the exact moments of
+// class 0 (k_pca_moments): N pixels, sums s, raw moments M;
+//     C[i][j] = (N M[i][j] - s_i s_j) / (N (N - 1))   (sample covariance)
+// with exact 128-bit numerators, then the same symmetric eigensolver (FP32
+// Jacobi + double-float refinement) on the B x B matrix, eigenvalues in
+// descending order, the same sign convention, and the same projection
+// coefficients, so every projection entry point applies to the result.
+// ---------------------------------------------------------------------------
+struct PcaSmem {
+    SymEig<MAXB> eig;
+    df V[MAXB][MAXB + 1];
+    df mu[MAXB];
+    df lam[MAXB];
+    int order[MAXB];
+    unsigned long long N;
+    float scale;
+};
+
+__global__ void __launch_bounds__(TPB) k_pca_finalize(DevModel* __restrict__ dm, int B, int nvec)
+{
+    extern __shared__ __align__(16) unsigned char pca_dyn[];
+    PcaSmem& sm = *reinterpret_cast<PcaSmem*>(pca_dyn);
+    const MomShape sh = mom_shape(B);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (dm->status != 0) return;
+    if (tid == 0) sm.N = mom_get(dm, sh, 0, B, B);
+    __syncthreads();
+    const unsigned long long N = sm.N;
+    if (N < 2) {
+        if (tid == 0) set_status(dm, CVA_ERR_EMPTY_CLASS);
+        return;
+    }
+    const df dN = df_from_u64(N);
+    const df inv_nn1 = df_rcp(df_from_u64(N * (N - 1)));  // N (N - 1) < 2^62
+    if (tid < B) sm.mu[tid] = df_div(df_from_u64(mom_get(dm, sh, 0, tid, B)), dN);
+    for (int q = tid; q < B * B; q += TPB) {
+        const int i = q / B, j = q - (q / B) * B;
+        if (i > j) continue;
+        const __int128 si = static_cast<__int128>(mom_get(dm, sh, 0, i, B));
+        const __int128 sj = static_cast<__int128>(mom_get(dm, sh, 0, j, B));
+        const __int128 num = static_cast<__int128>(N) * static_cast<__int128>(mom_get(dm, sh, 0, i, j)) - si * sj;
+        const df c = df_mul(df_from_i128(num), inv_nn1);
+        sm.eig.T[i][j] = c;
+        sm.eig.T[j][i] = c;
+    }
+    __syncthreads();
+    for (int q = tid; q < B * B; q += TPB) {  // covariance for the statistics getter
+        const int i = q / B, j = q - (q / B) * B;
+        dm->Sw[i][j] = df_to_double(sm.eig.T[i][j]);
+    }
+    if (warp == 0) {
+        float f = 0.0f;
+        for (int q = lane; q < B * B; q += 32) f = fmaf(sm.eig.T[q / B][q % B].hi, sm.eig.T[q / B][q % B].hi, f);
+        f = warp_sumf(f);
+        if (lane == 0) {
+            int ex = 0;
+            if (f > 0.0f) frexpf(sqrtf(f), &ex);
+            sm.scale = pow2f(-ex);
+        }
+    }
+    __syncthreads();
+    const float scale = sm.scale;
+    for (int q = tid; q < B * B; q += TPB) {
+        const int a = q / B, b = q % B;
+        sm.eig.T[a][b] = df_mulf(sm.eig.T[a][b], scale);  // exact: a power of two
+        sm.eig.Tf[a][b] = sm.eig.T[a][b].hi;
+        sm.eig.Wf[a][b] = (a == b) ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    sym_eig<MAXB>(sm.eig, B);
+    if (tid == 0) {
+        unsigned int used = 0u;
+        for (int j = 0; j < B; ++j) {
+            int best = -1;
+            for (int i = 0; i < B; ++i) {
+                if (used & (1u << i)) continue;
+                if (best < 0 || df_gt(sm.eig.lam[i], sm.eig.lam[best])) best = i;
+            }
+            used |= 1u << best;
+            sm.order[j] = best;
+        }
+    }
+    __syncthreads();
+    const int ncols = nvec > B ? B : nvec;
+    const float unscale = __frcp_rn(scale);  // a power of two: exact
+    if (tid < B) sm.lam[tid] = df_mulf(sm.eig.lam[sm.order[tid]], unscale);
+    for (int q = tid; q < B * ncols; q += TPB) {
+        const int b = q / ncols, j = q - (q / ncols) * ncols;
+        sm.V[b][j] = sm.eig.W[b][sm.order[j]];
+    }
+    __syncthreads();
+    // sign convention: the largest-magnitude component positive, lowest band on a tie
+    for (int j = warp; j < ncols; j += NWARP) {
+        const df v = lane < B ? sm.V[lane][j] : df_from(0.0f);
+        const df av = df_abs(v);
+        df big = av;
+        for (int o = 16; o > 0; o >>= 1) {
+            const df other = shfl_xor_df(big, o);
+            if (df_gt(other, big)) big = other;
+        }
+        const df thr = df_mul(big, df_make(1.0f, -static_cast<float>(TIE_REL)));
+        const unsigned ties = __ballot_sync(0xFFFFFFFFu, lane < B && df_ge(av, thr));
+        const int arg = __ffs(ties) - 1;
+        const float sh_hi = __shfl_sync(0xFFFFFFFFu, v.hi, arg);
+        const float sh_lo = __shfl_sync(0xFFFFFFFFu, v.lo, arg);
+        const bool neg = sh_hi < 0.0f || (sh_hi == 0.0f && sh_lo < 0.0f);
+        if (neg && lane < B) sm.V[lane][j] = df_neg(sm.V[lane][j]);
+    }
+    __syncthreads();
+    for (int q = tid; q < MAXB * MAXB; q += TPB) {
+        const int b = q / MAXB, j = q - (q / MAXB) * MAXB;
+        const bool live = b < B && j < ncols;
+        const double v = live ? df_to_double(sm.V[b][j]) : 0.0;
+        dm->V[b][j] = v;
+        dm->U[b][j] = v;
+        dm->Vf[b][j] = live ? sm.V[b][j].hi : 0.0f;
+    }
+    for (int q = tid; q < MAXB * MAXK; q += TPB) dm->Mb[q / MAXK][q % MAXK] = 0.0;
+    if (tid < MAXB) {
+        dm->lam[tid] = tid < B ? df_to_double(sm.lam[tid]) : 0.0;
+        dm->mu[tid] = tid < B ? df_to_double(sm.mu[tid]) : 0.0;
+        if (tid < B) dm->mu_c[0][tid] = dm->mu[tid];
+        const float m = tid < B ? rintf(sm.mu[tid].hi) : 0.0f;
+        dm->shift[tid] = MAGIC_2P23 + m;
+        dm->train_range[2 * tid] = __int_as_float(0x7F800000);       // +inf
+        dm->train_range[2 * tid + 1] = __int_as_float(0xFF800000);   // -inf
+    }
+    for (int j = warp; j < MAXB; j += NWARP) {
+        df s = df_from(0.0f);
+        if (j < ncols && lane < B) s = df_mul(sm.V[lane][j], df_sub(sm.mu[lane], df_from(rintf(sm.mu[lane].hi))));
+        if (j < ncols) s = warp_sum_df(s);
+        if (lane == 0) dm->dofs[j] = j < ncols ? s.hi : 0.0f;
+    }
+    if (tid == 0) {
+        dm->n[0] = static_cast<long long>(N);
+        dm->cls_count[0] = static_cast<unsigned int>(N);
+        dm->r = B;
+        dm->nvec = ncols;
+        dm->fitted = 1;
+    }
+}
+
 // Sb = Mb Mb^T for the statistics getter (not on the fit path).
 __global__ void k_scatter_sb(DevModel* __restrict__ dm, int B, int K)
 {
@@ -645,6 +823,15 @@ cudaError_t launch_batch_finalize(const PageDev* pages, int n, cudaStream_t s)
     cudaError_t e = cudaFuncSetAttribute(kb_fit_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kb_fit_finalize<<<static_cast<unsigned>(n), TPB, smem, s>>>(pages);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pca_finalize(DevModel* dm, int B, int nvec, cudaStream_t s)
+{
+    const int smem = static_cast<int>(sizeof(PcaSmem));
+    cudaError_t e = cudaFuncSetAttribute(k_pca_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_pca_finalize<<<1, TPB, smem, s>>>(dm, B, nvec);
     return cudaGetLastError();
 }
 

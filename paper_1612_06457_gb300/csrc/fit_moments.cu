@@ -439,38 +439,17 @@ __device__ __forceinline__ void moments_flush(DevModel* __restrict__ dm, int c, 
     }
 }
 
-// One unit: rows [row0, row0 + len) of the training matrix (row length F)
-// split into bytes, transposed into shared memory, its Gram matrix formed on
-// the tensor cores and added to the thread's moment sums.  Every thread of
-// the CTA takes part (three barriers).
-__device__ __forceinline__ void moments_unit(uint16_t* XT, float* Cs, const uint16_t* __restrict__ xtr, int F,
-                                             unsigned int row0, int len, int npair, const unsigned char* pa,
+// The Gram matrix of a staged unit (XT: the (2 F) x 256 split matrix [h ; l]
+// in shared memory) on the tensor cores, added to the thread's moment sums.
+// Every thread of the CTA takes part (two barriers; the caller synchronizes
+// after staging).
+__device__ __forceinline__ void moments_gram(const uint16_t* XT, float* Cs, int F, int npair, const unsigned char* pa,
                                              const unsigned char* pb, unsigned long long (&acc)[3])
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int F2 = 2 * F;
     const int MT = F2 / 16, NTL = F2 / 8;
-    // split and transpose: thread tid owns pixel column tid of the unit
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(xtr + static_cast<long long>(row0 + tid) * F);
-        #pragma unroll
-        for (int q = 0; q < (MAXB + 8) / 8; ++q) {
-            if (q * 8 < F) {
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (tid < len) v = __ldg(src + q);
-                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-                #pragma unroll
-                for (int h = 0; h < 8; ++h) {
-                    const uint32_t x = (wv[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
-                    const int f = q * 8 + h;
-                    XT[f * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x >> 8));
-                    XT[(F + f) * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x & 0xFFu));
-                }
-            }
-        }
-    }
-    __syncthreads();
-    // Gram matrix of the split unit, one 16 x 8 output tile per warp at a time
+    // one 16 x 8 output tile per warp at a time
     for (int t = warp; t < MT * NTL; t += NW) {
         const int mt = t / NTL, nt = t - (t / NTL) * NTL;
         // two independent accumulator chains (even and odd k steps); both
@@ -510,6 +489,38 @@ __device__ __forceinline__ void moments_unit(uint16_t* XT, float* Cs, const uint
         }
     }
     __syncthreads();
+}
+
+// One unit: rows [row0, row0 + len) of the training matrix (row length F)
+// split into bytes, transposed into shared memory, its Gram matrix formed on
+// the tensor cores and added to the thread's moment sums.  Every thread of
+// the CTA takes part (three barriers).
+__device__ __forceinline__ void moments_unit(uint16_t* XT, float* Cs, const uint16_t* __restrict__ xtr, int F,
+                                             unsigned int row0, int len, int npair, const unsigned char* pa,
+                                             const unsigned char* pb, unsigned long long (&acc)[3])
+{
+    const int tid = threadIdx.x;
+    // split and transpose: thread tid owns pixel column tid of the unit
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(xtr + static_cast<long long>(row0 + tid) * F);
+        #pragma unroll
+        for (int q = 0; q < (MAXB + 8) / 8; ++q) {
+            if (q * 8 < F) {
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (tid < len) v = __ldg(src + q);
+                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+                #pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                    const uint32_t x = (wv[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
+                    const int f = q * 8 + h;
+                    XT[f * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x >> 8));
+                    XT[(F + f) * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x & 0xFFu));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    moments_gram(XT, Cs, F, npair, pa, pb, acc);
 }
 
 // Exact moments on the tensor cores.  A unit holds up to 256 training rows of
@@ -695,6 +706,98 @@ kb_moments(const PageDev* __restrict__ pages, int n, const BatchTotals* __restri
         moments_flush(pages[cur_page].dm, cur_class, mom_shape(cur_b).nb, (cur_b + 1) * (cur_b + 2) / 2, pa, pb, acc);
 }
 
+// ---------------------------------------------------------------------------
+// Principal components (Section 2: the unsupervised PCA of the page): exact
+// moments of the augmented vectors (x, 1) of every selected pixel, straight
+// from the band-sequential cube, into class 0 of the model.  A unit is 256
+// consecutive pixels: with 16-byte-aligned rows each warp stages band rows
+// (8 pixels a lane, one 16-byte load), otherwise each thread stages one
+// pixel.  Masked-out pixels stage as zero columns and add nothing.
+// ---------------------------------------------------------------------------
+__device__ inline uint32_t pack_bf16_pair(uint32_t a, uint32_t b)
+{
+    return bf16_of_byte(a) | (bf16_of_byte(b) << 16);
+}
+
+__global__ void __launch_bounds__(TPB)
+k_pca_moments(const uint16_t* __restrict__ cube, int B, long long P, const uint8_t* __restrict__ mask, int vec,
+              DevModel* __restrict__ dm)
+{
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ unsigned char pa[MAXPAIR], pb[MAXPAIR];
+    const int F = xtr_row(B), BA = B + 1;
+    const int npair = BA * (BA + 1) / 2;
+    const int nb = mom_shape(B).nb;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint16_t* XT = reinterpret_cast<uint16_t*>(dyn);
+    float* Cs = reinterpret_cast<float*>(dyn + 2 * F * UPAD * 2);
+    build_pairs(pa, pb, BA);
+    __syncthreads();
+    unsigned long long acc[3] = {0ull, 0ull, 0ull};
+    const long long nunits = (P + UNIT - 1) / UNIT;
+    const long long per = (nunits + gridDim.x - 1) / gridDim.x;
+    const long long u0 = static_cast<long long>(blockIdx.x) * per;
+    const long long u1 = u0 + per < nunits ? u0 + per : nunits;
+    for (long long u = u0; u < u1; ++u) {
+        const long long p0 = u * UNIT;
+        if (vec) {
+            const long long pl = p0 + lane * 8;
+            const bool in = pl < P;  // P % 8 == 0: whole groups of 8
+            uint32_t sel = in ? 0xFFu : 0u;  // bit i: pixel pl + i selected
+            if (in && mask) {
+                const uint2 mv = *reinterpret_cast<const uint2*>(mask + pl);
+                sel = 0u;
+                #pragma unroll
+                for (int i = 0; i < 8; ++i) sel |= ((((i < 4 ? mv.x : mv.y) >> (8 * (i & 3))) & 0xFFu) != 0u) << i;
+            }
+            for (int f = warp; f < F; f += NW) {
+                uint32_t x[8];
+                if (f < B) {
+                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                    if (in) v = __ldcs(reinterpret_cast<const uint4*>(cube + static_cast<long long>(f) * P + pl));
+                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+                    #pragma unroll
+                    for (int i = 0; i < 8; ++i) x[i] = ((sel >> i) & 1u) ? ((wv[i >> 1] >> (16 * (i & 1))) & 0xFFFFu) : 0u;
+                } else {
+                    #pragma unroll
+                    for (int i = 0; i < 8; ++i) x[i] = (f == B) ? ((sel >> i) & 1u) : 0u;
+                }
+                const uint4 hi = make_uint4(pack_bf16_pair(x[0] >> 8, x[1] >> 8), pack_bf16_pair(x[2] >> 8, x[3] >> 8),
+                                            pack_bf16_pair(x[4] >> 8, x[5] >> 8), pack_bf16_pair(x[6] >> 8, x[7] >> 8));
+                const uint4 lo = make_uint4(pack_bf16_pair(x[0] & 0xFFu, x[1] & 0xFFu),
+                                            pack_bf16_pair(x[2] & 0xFFu, x[3] & 0xFFu),
+                                            pack_bf16_pair(x[4] & 0xFFu, x[5] & 0xFFu),
+                                            pack_bf16_pair(x[6] & 0xFFu, x[7] & 0xFFu));
+                *reinterpret_cast<uint4*>(XT + f * UPAD + lane * 8) = hi;
+                *reinterpret_cast<uint4*>(XT + (F + f) * UPAD + lane * 8) = lo;
+            }
+        } else {
+            const long long p = p0 + tid;
+            const bool sel = p < P && (!mask || mask[p] != 0);
+            for (int f = 0; f < F; ++f) {
+                uint32_t x = 0u;
+                if (sel) x = f < B ? static_cast<uint32_t>(cube[static_cast<long long>(f) * P + p]) : (f == B ? 1u : 0u);
+                XT[f * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x >> 8));
+                XT[(F + f) * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x & 0xFFu));
+            }
+        }
+        __syncthreads();
+        moments_gram(XT, Cs, F, npair, pa, pb, acc);
+    }
+    moments_flush(dm, 0, nb, npair, pa, pb, acc);
+}
+
+// Clears class 0's moments and the fit state before a principal-component fit.
+__global__ void k_pca_reset(DevModel* __restrict__ dm, int B)
+{
+    const MomShape sh = mom_shape(B);
+    for (int i = threadIdx.x; i < sh.nblk * 16; i += blockDim.x) dm->mom[0][i >> 4][i & 15] = 0ull;
+    if (threadIdx.x == 0) {
+        dm->status = CVA_OK;
+        dm->fitted = 0;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const uint8_t* labels, int K,
@@ -758,6 +861,29 @@ cudaError_t launch_batch_moments(const PageDev* pages, int n, const BatchTotals*
     cudaError_t e = cudaFuncSetAttribute(kb_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kb_moments<<<static_cast<unsigned>(num_sms * 4), TPB, smem, s>>>(pages, n, tot, xtr_pool, F);
+    return cudaGetLastError();
+}
+
+}  // namespace cva
+
+namespace cva {
+
+cudaError_t launch_pca_moments(const uint16_t* cube, int B, long long P, const uint8_t* mask, DevModel* dm,
+                               int num_sms, cudaStream_t s)
+{
+    const int vec = (P % 8 == 0) && (reinterpret_cast<uintptr_t>(cube) % 16 == 0) &&
+                    (!mask || reinterpret_cast<uintptr_t>(mask) % 8 == 0);
+    const int F2 = 2 * xtr_row(B);
+    const size_t smem = static_cast<size_t>(F2) * UPAD * 2 + static_cast<size_t>(F2) * F2 * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_pca_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_pca_reset<<<1, 256, 0, s>>>(dm, B);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long units = (P + UNIT - 1) / UNIT;
+    long long grid = static_cast<long long>(num_sms) * 4;
+    if (grid > units) grid = units;
+    k_pca_moments<<<static_cast<unsigned>(grid), TPB, smem, s>>>(cube, B, P, mask, vec, dm);
     return cudaGetLastError();
 }
 
