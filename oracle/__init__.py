@@ -74,6 +74,8 @@ def _load():
         lib.orc_to_u16.restype = None
         lib.orc_percentile_range.argtypes = [P, I64, I64, I64, P]
         lib.orc_pca_cov.argtypes = [P, I64, I64, P, P, P, P]
+        lib.orc_cluster_indices.argtypes = [P, I64, I64, P, I64, P, P, P, P, P, P]
+        lib.orc_cluster_indices.restype = ctypes.c_int
         lib.orc_pca_cov.restype = ctypes.c_int
         lib.orc_percentile_range.restype = ctypes.c_int
         for name in ("orc_class_sums", "orc_scatter", "orc_gen_eig", "orc_project"):
@@ -262,3 +264,44 @@ def pca(cube: np.ndarray, mask: Optional[np.ndarray] = None) -> Dict[str, np.nda
         raise OracleError(rc, "pca_cov")
     lam, V, sweeps = gen_eig(np.eye(B), C)
     return {"N": int(N.value), "mu": mu, "C": C, "lam": lam, "V": V, "sweeps": sweeps}
+
+
+def cluster_indices(y: np.ndarray, labels: np.ndarray, K: int) -> Dict[str, np.ndarray]:
+    """Section 3's cluster-separation indices of the labelled classes in a
+    k-band image y (k x P): counts T, centroids A (K x k), scatters S (eq. 1),
+    centroid distances M (eq. 2), Davies-Bouldin ratios R (eq. 3) and Dunn
+    indices DI (eq. 5), the last three K x K."""
+    lib = _load()
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    if y.ndim == 1:
+        y = y[None, :]
+    k, P = y.shape
+    labels = np.ascontiguousarray(labels, dtype=np.uint8).reshape(-1)
+    if labels.size != P:
+        raise ValueError("labels must have one entry per pixel")
+    T = np.zeros(K, np.int64)
+    A = np.zeros((K, k))
+    S = np.zeros(K)
+    M = np.zeros((K, K))
+    R = np.zeros((K, K))
+    DI = np.zeros((K, K))
+    rc = lib.orc_cluster_indices(_ptr(y), k, P, _ptr(labels), K, _ptr(T), _ptr(A), _ptr(S), _ptr(M), _ptr(R),
+                                 _ptr(DI))
+    if rc != OK:
+        raise OracleError(rc, "cluster_indices")
+    return {"T": T, "A": A, "S": S, "M": M, "R": R, "DI": DI}
+
+
+def rgb_composite(planes: np.ndarray, src, invert=(False, False, False)) -> np.ndarray:
+    """The colour image of Section 2 / Figure 5: three 8-bit images as the
+    red, green and blue channels (planes[src[c]] for channel c, optionally
+    inverted as 255 - v), interleaved H x W x 3."""
+    planes = np.asarray(planes, dtype=np.uint8)
+    k = planes.shape[0]
+    out = np.zeros(planes.shape[1:] + (3,), np.uint8)
+    for c in range(3):
+        if not 0 <= src[c] < k:
+            raise ValueError("channel source out of range")
+        v = planes[src[c]]
+        out[..., c] = (255 - v) if invert[c] else v
+    return out

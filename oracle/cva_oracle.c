@@ -458,3 +458,67 @@ int orc_pca_cov(const uint16_t* cube, int64_t B, int64_t P, const uint8_t* mask,
     for (int64_t i = 0; i < B * B; ++i) C[i] /= (double)(N - 1);
     return ORC_OK;
 }
+
+
+/* Cluster-separation indices of the classes of a label map in a k-band image
+ * (Section 3, eqs. 1-5; p = 2): for class c with T_c labelled pixels x,
+ *   A_c  = the centroid (mean of x),
+ *   S_c  = the mean Euclidean distance of its pixels to A_c          (eq. 1)
+ * and for a pair of classes
+ *   M_ij = ||A_i - A_j||                                             (eq. 2)
+ *   R_ij = (S_i + S_j) / M_ij          (Davies-Bouldin ratio,        eq. 3)
+ *   DI_ij = (M_ij - S_i - S_j) / max(S_i, S_j)    (Dunn,             eq. 5)
+ * y is k x P (doubles), labels P (0 = none, c + 1 = class c).  M, R and DI are
+ * K x K; their diagonals are 0; R is +inf when M_ij = 0 and DI is +inf when
+ * both scatters are 0. */
+int orc_cluster_indices(const double* y, int64_t k, int64_t P, const uint8_t* labels, int64_t K, int64_t* T,
+                        double* A, double* S, double* M, double* R, double* DI)
+{
+    if (k < 1 || P < 0 || K < 1) return ORC_ERR_ARG;
+    for (int64_t c = 0; c < K; ++c) {
+        T[c] = 0;
+        S[c] = 0.0;
+        for (int64_t j = 0; j < k; ++j) A[c * k + j] = 0.0;
+    }
+    for (int64_t p = 0; p < P; ++p) {
+        const int64_t lab = labels[p];
+        if (lab == 0) continue;
+        if (lab > K) return ORC_ERR_LABEL;
+        T[lab - 1] += 1;
+        for (int64_t j = 0; j < k; ++j) A[(lab - 1) * k + j] += y[j * P + p];
+    }
+    for (int64_t c = 0; c < K; ++c) {
+        if (T[c] == 0) return ORC_ERR_EMPTY_CLASS;
+        for (int64_t j = 0; j < k; ++j) A[c * k + j] /= (double)T[c];
+    }
+    for (int64_t p = 0; p < P; ++p) {
+        const int64_t lab = labels[p];
+        if (lab == 0) continue;
+        double d2 = 0.0;
+        for (int64_t j = 0; j < k; ++j) {
+            const double d = y[j * P + p] - A[(lab - 1) * k + j];
+            d2 += d * d;
+        }
+        S[lab - 1] += sqrt(d2);
+    }
+    for (int64_t c = 0; c < K; ++c) S[c] /= (double)T[c];
+    for (int64_t i = 0; i < K; ++i)
+        for (int64_t j = 0; j < K; ++j) {
+            double d2 = 0.0;
+            for (int64_t q = 0; q < k; ++q) {
+                const double d = A[i * k + q] - A[j * k + q];
+                d2 += d * d;
+            }
+            const double m = sqrt(d2);
+            M[i * K + j] = m;
+            if (i == j) {
+                R[i * K + j] = 0.0;
+                DI[i * K + j] = 0.0;
+                continue;
+            }
+            R[i * K + j] = m > 0.0 ? (S[i] + S[j]) / m : INFINITY;
+            const double smax = S[i] > S[j] ? S[i] : S[j];
+            DI[i * K + j] = smax > 0.0 ? (m - S[i] - S[j]) / smax : INFINITY;
+        }
+    return ORC_OK;
+}

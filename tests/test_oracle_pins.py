@@ -473,9 +473,63 @@ def test_error_cases():
 # --------------------------------------------------------------------------
 
 def _dbi(a, b):
-    Sa = np.mean(np.abs(a - a.mean()))
-    Sb = np.mean(np.abs(b - b.mean()))
-    return (Sa + Sb) / abs(a.mean() - b.mean())
+    """Eq. 3 for two one-dimensional clusters, through the oracle."""
+    y = np.concatenate([a, b])[None, :]
+    labels = np.concatenate([np.ones(a.size), 2 * np.ones(b.size)]).astype(np.uint8)
+    return oracle.cluster_indices(y, labels, 2)["R"][0, 1]
+
+
+def test_cluster_indices_hand_solved_one_band():
+    """Class 1 = {0, 2}: centroid 1, scatter 1.  Class 2 = {10, 14}: centroid
+    12, scatter 2.  M = 11, R = 3/11 (eq. 3), DI = (11 - 3)/2 = 4 (eq. 5)."""
+    y = np.array([[0.0, 10.0, 2.0, 14.0, 99.0]])
+    labels = np.array([1, 2, 1, 2, 0], np.uint8)
+    r = oracle.cluster_indices(y, labels, 2)
+    np.testing.assert_array_equal(r["T"], [2, 2])
+    np.testing.assert_array_equal(r["A"][:, 0], [1.0, 12.0])
+    np.testing.assert_array_equal(r["S"], [1.0, 2.0])
+    assert r["M"][0, 1] == 11.0 and r["M"][1, 0] == 11.0
+    assert r["R"][0, 1] == pytest.approx(3.0 / 11.0, rel=1e-15)
+    assert r["DI"][0, 1] == 4.0
+    assert r["R"][0, 0] == 0.0 and r["DI"][1, 1] == 0.0
+
+
+def test_cluster_indices_hand_solved_two_bands():
+    """{(0,0), (0,2)}: centroid (0,1), scatter 1; {(3,1), (5,1)}: centroid
+    (4,1), scatter 1; M = 4, R = 1/2, DI = (4 - 2)/1 = 2; a third class
+    {(0,1)} has scatter 0 and the same centroid as the first: R = inf."""
+    y = np.array([[0.0, 0.0, 3.0, 5.0, 0.0], [0.0, 2.0, 1.0, 1.0, 1.0]])
+    labels = np.array([1, 1, 2, 2, 3], np.uint8)
+    r = oracle.cluster_indices(y, labels, 3)
+    np.testing.assert_array_equal(r["A"], [[0.0, 1.0], [4.0, 1.0], [0.0, 1.0]])
+    np.testing.assert_array_equal(r["S"], [1.0, 1.0, 0.0])
+    assert r["R"][0, 1] == 0.5 and r["DI"][0, 1] == 2.0
+    assert np.isinf(r["R"][0, 2])
+
+
+def test_cluster_indices_invariances():
+    rng = np.random.default_rng(44)
+    y = rng.normal(size=(3, 400))
+    labels = rng.integers(0, 4, size=400).astype(np.uint8)
+    r = oracle.cluster_indices(y, labels, 3)
+    rs = oracle.cluster_indices(7.5 * y + 3.0, labels, 3)      # scale and shift of the image
+    np.testing.assert_allclose(rs["R"], r["R"], rtol=1e-12)
+    np.testing.assert_allclose(rs["DI"], r["DI"], rtol=1e-12, atol=1e-12)
+    rp = oracle.cluster_indices(y[[2, 0, 1]], labels, 3)       # band order
+    np.testing.assert_allclose(rp["R"], r["R"], rtol=1e-12)
+    perm = np.array([0, 3, 1, 2], np.uint8)                     # class order: 1->3, 2->1, 3->2
+    rc = oracle.cluster_indices(y, perm[labels], 3)
+    np.testing.assert_allclose(rc["R"][np.ix_([2, 0, 1], [2, 0, 1])], r["R"], rtol=1e-12)
+    with pytest.raises(oracle.OracleError):
+        oracle.cluster_indices(y, np.zeros(400, np.uint8), 2)   # empty classes
+
+
+def test_rgb_composite_hand_example():
+    planes = np.array([[[10, 20]], [[30, 40]], [[50, 60]]], np.uint8)  # 3 planes of 1 x 2
+    rgb = oracle.rgb_composite(planes, (2, 0, 1))
+    assert rgb.tolist() == [[[50, 10, 30], [60, 20, 40]]]
+    rgb = oracle.rgb_composite(planes, (0, 0, 2), invert=(True, False, True))
+    assert rgb.tolist() == [[[245, 10, 205], [235, 20, 195]]]
 
 
 def test_cva_image_separates_undertext_better_than_any_band():
