@@ -222,6 +222,39 @@ int cva_percentile_range(const float* proj, int k, int H, int W, double percent,
 int cva_to_u16(const float* proj, int k, int H, int W, int mode, const float* range,
                cva_model* m, uint16_t* out, void* stream);
 
+/* Element types of an image given to cva_cluster_indices. */
+#define CVA_IMAGE_U8 0   /* uint8 planes (the 8-bit images) */
+#define CVA_IMAGE_F32 1  /* float32 planes (the projections) */
+
+/* Cluster-separation indices of the labelled classes in a k-band image
+ * (Section 3, eqs. 1-5, with p = 2): for each class c its labelled pixel
+ * count T_c, centroid A_c and scatter S_c (mean Euclidean distance of its
+ * pixels to A_c, eq. 1); for each pair the centroid distance M_ij (eq. 2),
+ * the Davies-Bouldin ratio R_ij = (S_i + S_j) / M_ij (eq. 3) and the Dunn
+ * index DI_ij = (M_ij - S_i - S_j) / max(S_i, S_j) (eq. 5).  Diagonals are 0;
+ * R is +inf when two centroids coincide and DI when both scatters are 0.
+ *   image   device, k x H x W planes of `dtype`
+ *   labels  device, H x W uint8 (0 = not used, c + 1 = class c)
+ *   m       any model on this device (its evaluation scratch is used)
+ *   counts (K), centroids (K x k), scatter (K), M, R, DI (K x K): host
+ *           outputs, row-major, each may be NULL
+ * Synchronizes `stream`.  Returns CVA_ERR_LABEL_RANGE for a label above K
+ * and CVA_ERR_EMPTY_CLASS for a class without pixels. */
+int cva_cluster_indices(const void* image, int dtype, int k, int H, int W, const uint8_t* labels, int K,
+                        cva_model* m, int64_t* counts, double* centroids, double* scatter, double* M,
+                        double* R, double* DI, void* stream);
+
+/* Colour image from three of k 8-bit images (Section 2 / Figure 5: three
+ * grayscale images as the red, green and blue channels, the one with the
+ * clearest undertext usually in green; Figure 5 also inverts channels):
+ * rgb[3 p + c] = planes[src[c]][p], or 255 minus it when bit c of `invert`
+ * is set.
+ *   planes  device, k x H x W uint8;  src  host, 3 plane indices (R, G, B)
+ *   rgb     device, H x W x 3 uint8 (interleaved)
+ * Asynchronous; one pass. */
+int cva_rgb_composite(const uint8_t* planes, int k, int H, int W, const int* src, int invert, uint8_t* rgb,
+                      void* stream);
+
 /* Fused projection and 8-bit rescale: one pass over the cube for
  * CVA_RANGE_TRAINING and CVA_RANGE_GIVEN, two passes (range, then
  * projection) for CVA_RANGE_GLOBAL.

@@ -54,6 +54,8 @@ SIGNATURES = {
     "cva_to_u8": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "cva_project_u8": (_I, [_P, _I, _I, _I, _P, _I, _I, _P, _P, _P]),
     "cva_pca_fit": (_I, [_P, _I, _I, _I, _P, _P, _P]),
+    "cva_cluster_indices": (_I, [_P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "cva_rgb_composite": (_I, [_P, _I, _I, _I, _P, _I, _P, _P]),
     "cva_percentile_range": (_I, [_P, _I, _I, _I, ctypes.c_double, _P, _P, _P]),
     "cva_to_u16": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "cva_fit_project_u8_noalloc": (_I, [_P, _I, _I, _I, _P, _I, _I, _P, _P, _P, _P]),
@@ -363,3 +365,38 @@ def cva_pca_fit(cube: torch.Tensor, m: Model, mask: Optional[torch.Tensor] = Non
         raise ValueError("mask must be H x W")
     _check(load().cva_pca_fit(_dptr(cube, torch.uint16, "cube"), B, H, W, _dptr(mask, torch.uint8, "mask"),
                               m.handle, _stream_ptr(stream)), "cva_pca_fit")
+
+
+CVA_IMAGE_U8 = 0
+CVA_IMAGE_F32 = 1
+
+
+def cva_cluster_indices(image: torch.Tensor, labels: torch.Tensor, K: int, m: Model, stream=None):
+    """Section 3's indices of the labelled classes in ``image`` (k x H x W,
+    uint8 or float32).  Returns a dict of numpy arrays T, A, S, M, R, DI."""
+    import numpy as np
+
+    k, H, W = image.shape
+    if image.dtype == torch.uint8:
+        dtype, ptr = CVA_IMAGE_U8, _dptr(image, torch.uint8, "image")
+    else:
+        dtype, ptr = CVA_IMAGE_F32, _dptr(image, torch.float32, "image")
+    T = np.zeros(K, np.int64)
+    A = np.zeros((K, k))
+    S = np.zeros(K)
+    M = np.zeros((K, K))
+    R = np.zeros((K, K))
+    DI = np.zeros((K, K))
+    _check(load().cva_cluster_indices(ptr, dtype, k, H, W, _dptr(labels, torch.uint8, "labels"), K, m.handle,
+                                      _hptr(T), _hptr(A), _hptr(S), _hptr(M), _hptr(R), _hptr(DI),
+                                      _stream_ptr(stream)), "cva_cluster_indices")
+    return {"T": T, "A": A, "S": S, "M": M, "R": R, "DI": DI}
+
+
+def cva_rgb_composite(planes: torch.Tensor, src, out: torch.Tensor, invert=(False, False, False), stream=None) -> None:
+    """Interleaved H x W x 3 colour image from planes[src[0..2]] (see cva.h)."""
+    k, H, W = planes.shape
+    s3 = (ctypes.c_int * 3)(*[int(x) for x in src])
+    inv = sum(1 << c for c in range(3) if invert[c])
+    _check(load().cva_rgb_composite(_dptr(planes, torch.uint8, "planes"), k, H, W, s3, inv,
+                                    _dptr(out, torch.uint8, "out"), _stream_ptr(stream)), "cva_rgb_composite")

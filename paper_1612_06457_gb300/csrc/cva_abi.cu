@@ -428,6 +428,61 @@ int cva_to_u16(const float* proj, int k, int H, int W, int mode, const float* ra
     return from_cuda(e);
 }
 
+int cva_cluster_indices(const void* image, int dtype, int k, int H, int W, const uint8_t* labels, int K, cva_model* m,
+                        int64_t* counts, double* centroids, double* scatter, double* M, double* R, double* DI,
+                        void* stream)
+{
+    if (!m || !image || !labels || k < 1 || k > CVA_MAX_BANDS || K < 1 || K > CVA_MAX_CLASSES || H < 1 || W < 1)
+        return CVA_ERR_INVALID_ARG;
+    if (dtype != CVA_IMAGE_U8 && dtype != CVA_IMAGE_F32) return CVA_ERR_INVALID_ARG;
+    const long long P = static_cast<long long>(H) * W;
+    if (P >= (1LL << 31)) return CVA_ERR_INVALID_ARG;
+    if (dtype == CVA_IMAGE_F32 && reinterpret_cast<uintptr_t>(image) % 4 != 0) return CVA_ERR_INVALID_ARG;
+    if (!device_visible(image) || !device_visible(labels)) return CVA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevModel* dm = m->dm;
+    cudaError_t e = cva::launch_cluster_indices(dtype == CVA_IMAGE_U8 ? static_cast<const uint8_t*>(image) : nullptr,
+                                                dtype == CVA_IMAGE_F32 ? static_cast<const float*>(image) : nullptr,
+                                                k, P, labels, K, dm, m->num_sms, s);
+    if (e != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return CVA_ERR_CUDA;
+    int st = 0;
+    if (cudaMemcpy(&st, &dm->ev_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CVA_ERR_CUDA;
+    if (st != CVA_OK) return st;
+    if (counts) {
+        unsigned long long c[cva::MAXK];
+        if (cudaMemcpy(c, dm->ev_count, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return CVA_ERR_CUDA;
+        for (int i = 0; i < K; ++i) counts[i] = static_cast<int64_t>(c[i]);
+    }
+    if (centroids && cudaMemcpy2D(centroids, sizeof(double) * k, dm->ev_sum, sizeof(double) * cva::MAXB,
+                                  sizeof(double) * k, K, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    if (scatter && cudaMemcpy(scatter, dm->ev_scatter, sizeof(double) * K, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    const double* tables[3] = {&dm->ev_M[0][0], &dm->ev_R[0][0], &dm->ev_DI[0][0]};
+    double* outs[3] = {M, R, DI};
+    for (int t = 0; t < 3; ++t)
+        if (outs[t] && cudaMemcpy2D(outs[t], sizeof(double) * K, tables[t], sizeof(double) * cva::MAXK,
+                                    sizeof(double) * K, K, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return CVA_ERR_CUDA;
+    return CVA_OK;
+}
+
+int cva_rgb_composite(const uint8_t* planes, int k, int H, int W, const int* src, int invert, uint8_t* rgb,
+                      void* stream)
+{
+    if (!planes || !src || !rgb || k < 1 || H < 1 || W < 1 || invert < 0 || invert > 7) return CVA_ERR_INVALID_ARG;
+    const long long P = static_cast<long long>(H) * W;
+    if (P >= (1LL << 31)) return CVA_ERR_INVALID_ARG;
+    for (int c = 0; c < 3; ++c)
+        if (src[c] < 0 || src[c] >= k) return CVA_ERR_INVALID_ARG;
+    if (!device_visible(planes) || !device_visible(rgb)) return CVA_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CVA_ERR_CUDA;
+    return from_cuda(cva::launch_rgb_composite(planes, P, src[0], src[1], src[2], invert, rgb, sms,
+                                               static_cast<cudaStream_t>(stream)));
+}
+
 int cva_project_u8(const uint16_t* cube, int B, int H, int W, cva_model* m, int k, int mode, const float* range,
                    uint8_t* out, void* stream)
 {

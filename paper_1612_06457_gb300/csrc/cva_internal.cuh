@@ -98,6 +98,15 @@ struct DevModel {
     // ---- order statistics of the third rescale ------------------------------
     unsigned int sel_prefix[2 * MAXB];  // known leading key bits of (lo, hi) of each variate
     unsigned int sel_rank[2 * MAXB];    // rank still to find among the keys with that prefix
+
+    // ---- cluster-separation indices (Section 3) -----------------------------
+    int ev_status;                      // CVA_OK or the evaluation's error
+    unsigned long long ev_count[MAXK];  // labelled pixels per class
+    double ev_sum[MAXK][MAXB];          // sums, then centroids
+    double ev_scatter[MAXK];            // sums of distances, then scatters
+    double ev_M[MAXK][MAXK];
+    double ev_R[MAXK][MAXK];
+    double ev_DI[MAXK][MAXK];
 };
 
 // -------------------------------------------------------------------------
@@ -137,6 +146,15 @@ cudaError_t launch_f32_to_u8(const float* proj, int k, long long P, const DevMod
 cudaError_t launch_pca_moments(const uint16_t* cube, int B, long long P, const uint8_t* mask, DevModel* dm,
                                int num_sms, cudaStream_t s);
 cudaError_t launch_pca_finalize(DevModel* dm, int B, int nvec, cudaStream_t s);
+
+// Cluster-separation indices of the labelled classes of a k-band image
+// (uint8 when f32 is null) into the model's ev_* fields.
+cudaError_t launch_cluster_indices(const uint8_t* img_u8, const float* img_f32, int k, long long P,
+                                   const uint8_t* labels, int K, DevModel* dm, int num_sms, cudaStream_t s);
+// Interleaved RGB image from three of k planes (src: plane of R, G, B;
+// invert: bit c inverts channel c).
+cudaError_t launch_rgb_composite(const uint8_t* planes, long long P, int s0, int s1, int s2, int invert,
+                                 uint8_t* rgb, int num_sms, cudaStream_t s);
 
 // Third rescale: lo / hi of each of k projections with m values taken out of
 // each tail (`hist`: 2 x 2048 words per variate, zero on entry and on exit).
