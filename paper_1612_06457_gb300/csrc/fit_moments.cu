@@ -449,9 +449,12 @@ __device__ __forceinline__ void moments_gram(const uint16_t* XT, float* Cs, int 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int F2 = 2 * F;
     const int MT = F2 / 16, NTL = F2 / 8;
-    // one 16 x 8 output tile per warp at a time
+    // one 16 x 8 output tile per warp at a time; the Gram matrix is
+    // symmetric and only entries on or above the diagonal are read, so
+    // tiles wholly below it are skipped
     for (int t = warp; t < MT * NTL; t += NW) {
         const int mt = t / NTL, nt = t - (t / NTL) * NTL;
+        if (nt * 8 + 7 < mt * 16) continue;
         // two independent accumulator chains (even and odd k steps); both
         // hold integers below 2^24, so their sum is exact as well
         float d[4] = {0.0f, 0.0f, 0.0f, 0.0f}, e[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -483,7 +486,7 @@ __device__ __forceinline__ void moments_gram(const uint16_t* XT, float* Cs, int 
             const int a = pa[q], b = pb[q];
             const unsigned long long hh = __float2uint_rn(Cs[a * F2 + b]);
             const unsigned long long hl = __float2uint_rn(Cs[a * F2 + F + b]);
-            const unsigned long long lh = __float2uint_rn(Cs[(F + a) * F2 + b]);
+            const unsigned long long lh = __float2uint_rn(Cs[b * F2 + F + a]);  // = C[F + a][b] by symmetry
             const unsigned long long ll = __float2uint_rn(Cs[(F + a) * F2 + F + b]);
             acc[k] += (hh << 16) + ((hl + lh) << 8) + ll;
         }
@@ -738,29 +741,43 @@ k_pca_moments(const uint16_t* __restrict__ cube, int B, long long P, const uint8
     const long long per = (nunits + gridDim.x - 1) / gridDim.x;
     const long long u0 = static_cast<long long>(blockIdx.x) * per;
     const long long u1 = u0 + per < nunits ? u0 + per : nunits;
-    for (long long u = u0; u < u1; ++u) {
-        const long long p0 = u * UNIT;
-        if (vec) {
-            const long long pl = p0 + lane * 8;
+    if (vec) {
+        // software pipeline: the 16-byte band loads of unit u + 1 are issued
+        // before the Gram matrix of unit u is formed
+        constexpr int ROWS = (MAXB + 8 + NW - 1) / NW;  // rows f = warp + r NW a warp stages: 5 cover F <= 40
+        uint4 nx[ROWS];
+        uint32_t nsel = 0u;
+        auto load_unit = [&](long long u) {
+            const long long pl = u * UNIT + lane * 8;
             const bool in = pl < P;  // P % 8 == 0: whole groups of 8
-            uint32_t sel = in ? 0xFFu : 0u;  // bit i: pixel pl + i selected
+            nsel = in ? 0xFFu : 0u;  // bit i: pixel pl + i selected
             if (in && mask) {
                 const uint2 mv = *reinterpret_cast<const uint2*>(mask + pl);
-                sel = 0u;
+                nsel = 0u;
                 #pragma unroll
-                for (int i = 0; i < 8; ++i) sel |= ((((i < 4 ? mv.x : mv.y) >> (8 * (i & 3))) & 0xFFu) != 0u) << i;
+                for (int i = 0; i < 8; ++i) nsel |= ((((i < 4 ? mv.x : mv.y) >> (8 * (i & 3))) & 0xFFu) != 0u) << i;
             }
-            for (int f = warp; f < F; f += NW) {
+            #pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const int f = warp + r * NW;
+                nx[r] = make_uint4(0u, 0u, 0u, 0u);
+                if (in && f < B) nx[r] = __ldcs(reinterpret_cast<const uint4*>(cube + static_cast<long long>(f) * P + pl));
+            }
+        };
+        if (u0 < u1) load_unit(u0);
+        for (long long u = u0; u < u1; ++u) {
+            #pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const int f = warp + r * NW;
+                if (f >= F) break;
                 uint32_t x[8];
                 if (f < B) {
-                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                    if (in) v = __ldcs(reinterpret_cast<const uint4*>(cube + static_cast<long long>(f) * P + pl));
-                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+                    const uint32_t wv[4] = {nx[r].x, nx[r].y, nx[r].z, nx[r].w};
                     #pragma unroll
-                    for (int i = 0; i < 8; ++i) x[i] = ((sel >> i) & 1u) ? ((wv[i >> 1] >> (16 * (i & 1))) & 0xFFFFu) : 0u;
+                    for (int i = 0; i < 8; ++i) x[i] = ((nsel >> i) & 1u) ? ((wv[i >> 1] >> (16 * (i & 1))) & 0xFFFFu) : 0u;
                 } else {
                     #pragma unroll
-                    for (int i = 0; i < 8; ++i) x[i] = (f == B) ? ((sel >> i) & 1u) : 0u;
+                    for (int i = 0; i < 8; ++i) x[i] = (f == B) ? ((nsel >> i) & 1u) : 0u;
                 }
                 const uint4 hi = make_uint4(pack_bf16_pair(x[0] >> 8, x[1] >> 8), pack_bf16_pair(x[2] >> 8, x[3] >> 8),
                                             pack_bf16_pair(x[4] >> 8, x[5] >> 8), pack_bf16_pair(x[6] >> 8, x[7] >> 8));
@@ -771,7 +788,13 @@ k_pca_moments(const uint16_t* __restrict__ cube, int B, long long P, const uint8
                 *reinterpret_cast<uint4*>(XT + f * UPAD + lane * 8) = hi;
                 *reinterpret_cast<uint4*>(XT + (F + f) * UPAD + lane * 8) = lo;
             }
-        } else {
+            __syncthreads();
+            if (u + 1 < u1) load_unit(u + 1);
+            moments_gram(XT, Cs, F, npair, pa, pb, acc);
+        }
+    } else {
+        for (long long u = u0; u < u1; ++u) {
+            const long long p0 = u * UNIT;
             const long long p = p0 + tid;
             const bool sel = p < P && (!mask || mask[p] != 0);
             for (int f = 0; f < F; ++f) {
@@ -780,9 +803,9 @@ k_pca_moments(const uint16_t* __restrict__ cube, int B, long long P, const uint8
                 XT[f * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x >> 8));
                 XT[(F + f) * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x & 0xFFu));
             }
+            __syncthreads();
+            moments_gram(XT, Cs, F, npair, pa, pb, acc);
         }
-        __syncthreads();
-        moments_gram(XT, Cs, F, npair, pa, pb, acc);
     }
     moments_flush(dm, 0, nb, npair, pa, pb, acc);
 }
@@ -881,7 +904,7 @@ cudaError_t launch_pca_moments(const uint16_t* cube, int B, long long P, const u
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long units = (P + UNIT - 1) / UNIT;
-    long long grid = static_cast<long long>(num_sms) * 4;
+    long long grid = static_cast<long long>(num_sms) * 6;
     if (grid > units) grid = units;
     k_pca_moments<<<static_cast<unsigned>(grid), TPB, smem, s>>>(cube, B, P, mask, vec, dm);
     return cudaGetLastError();
