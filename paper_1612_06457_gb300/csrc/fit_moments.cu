@@ -9,9 +9,9 @@
 // depend on the order of accumulation, so the result is deterministic even
 // though thread blocks merge their partial sums with atomics.
 //
-// Four kernels; the label map is cut into tiles of 16384 labels, one CTA per
-// tile in the label passes (each thread holds 64 labels from four 128-bit
-// loads in flight, compared four bytes at a time):
+// Four kernels for one page; the label map is cut into tiles of 16384
+// labels, one CTA per tile in the label passes (each thread holds 64 labels
+// from four 128-bit loads in flight, compared four bytes at a time):
 //   k_tile_count    training pixels of each class in the tile, and whether
 //                   the tile holds a label above K; the last CTA to finish
 //                   (atomic ticket, no waiting) then takes the prefix sums of
@@ -32,6 +32,9 @@
 //                   registers while a CTA stays on one class and are merged
 //                   into the model with 64-bit integer atomics when it moves
 //                   on.  The "1" column yields n_c and s_c in the same pass.
+// The same passes in batched form (kb_*: the flattened work of many pages,
+// see batch.cu), and the moments of every selected pixel of a page for the
+// principal components (k_pca_moments, straight from the cube).
 #include "cva_internal.cuh"
 
 namespace cva {

@@ -23,7 +23,9 @@
 //
 // The training-range kernel repeats the same FP32 operations, in the same
 // order, on the training pixels, so that the extreme training pixels land on
-// exactly 0 and 255 in the fused projection.
+// exactly 0 and 255 in the fused projection.  The batched kernels
+// (kb_train_range, kb_project_v8) run the same per-pixel code over the
+// flattened work of many pages (see batch.cu).
 #include "cva_internal.cuh"
 
 namespace cva {
@@ -65,22 +67,6 @@ __device__ inline void load_coefs(ProjSmem<KV>& sm, const DevModel* dm, int B, i
         const float sc = code_scale(lo, hi);
         sm.scale[tid] = sc;
         sm.off[tid] = code_offset(lo, sc);
-    }
-}
-
-template <int KV>
-__device__ inline void accumulate4(float (&acc)[KV][4], const uint2& w, const float* vrow, float shift)
-{
-    float x[4];
-    x[0] = __fsub_rn(u16_lo_biased(w.x), shift);
-    x[1] = __fsub_rn(u16_hi_biased(w.x), shift);
-    x[2] = __fsub_rn(u16_lo_biased(w.y), shift);
-    x[3] = __fsub_rn(u16_hi_biased(w.y), shift);
-    #pragma unroll
-    for (int j = 0; j < KV; ++j) {
-        const float v = vrow[j];
-        #pragma unroll
-        for (int i = 0; i < 4; ++i) acc[j][i] = __fmaf_rn(v, x[i], acc[j][i]);
     }
 }
 
