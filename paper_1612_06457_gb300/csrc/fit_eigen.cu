@@ -142,91 +142,127 @@ __device__ inline float block_maxf(SymEig<NM>& e, float v, int slot)
     return m;
 }
 
+// Sum over the team: warp 0 (TEAM = 32) or the whole block (TEAM = TPB).
+template <int NM, int TEAM>
+__device__ inline float team_sumf(SymEig<NM>& e, float v)
+{
+    v = warp_sumf(v);
+    if (TEAM == 32) return v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) e.red[0][warp] = v;
+    __syncthreads();
+    float t = 0.0f;
+    for (int w = 0; w < NWARP; ++w) t += e.red[0][w];
+    __syncthreads();  // the scratch row is free again
+    return t;
+}
+
+template <int TEAM>
+__device__ inline void team_sync()
+{
+    if (TEAM == 32) __syncwarp();
+    else __syncthreads();
+}
+
+// Cyclic Jacobi on e.Tf (round-robin order) in FP32, accumulating the
+// rotations in e.Wf.  Run by warp 0 alone for small orders (TEAM = 32) or by
+// the whole block (TEAM = TPB), which applies the rotations of a round in
+// parallel over all its threads.
+template <int NM, int TEAM>
+__device__ void jacobi_team(SymEig<NM>& e, int n)
+{
+    const int me = TEAM == 32 ? static_cast<int>(threadIdx.x & 31) : static_cast<int>(threadIdx.x);
+    const int m = n + (n & 1), half = m / 2;
+    for (int q = me; q < (m - 1) * m; q += TEAM) {  // round-robin seating, one row per round
+        const int round = q / m, seat = q - (q / m) * m;
+        e.rr[round][seat] = static_cast<unsigned char>(rr_player(seat, round, m));
+    }
+    float tot = 0.0f;
+    for (int q = me; q < n * n; q += TEAM) tot = fmaf(e.Tf[q / n][q % n], e.Tf[q / n][q % n], tot);
+    tot = team_sumf<NM, TEAM>(e, tot);
+    team_sync<TEAM>();
+    float prev = 3.0e38f;
+    for (int sweep = 0; sweep < JACOBI_SWEEPS; ++sweep) {
+        float off = 0.0f;
+        for (int q = me; q < n * n; q += TEAM) {
+            const int a = q / n, b = q % n;
+            if (a != b) off = fmaf(e.Tf[a][b], e.Tf[a][b], off);
+        }
+        off = team_sumf<NM, TEAM>(e, off);
+        if (off <= 1e-11f * tot || off >= 0.25f * prev) break;  // converged, or stalled at FP32 rounding
+        prev = off;
+        for (int round = 0; round < m - 1; ++round) {
+            if (me < half) {
+                const int a = e.rr[round][me], b = e.rr[round][m - 1 - me];
+                const int p = min(a, b), q = max(a, b);
+                int ok = 0;
+                float cs = 1.0f, sn = 0.0f;
+                if (q < n) {
+                    const float apq = e.Tf[p][q];
+                    if (apq != 0.0f) {
+                        // approximate intrinsics suffice: the refinement below
+                        // restores accuracy, only orthogonal-enough rotations matter
+                        const float tau = __fdividef(e.Tf[q][q] - e.Tf[p][p], 2.0f * apq);
+                        float t;
+                        if (fabsf(tau) > 1e15f) t = __fdividef(0.5f, tau);
+                        else t = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.0f))), tau);
+                        cs = rsqrtf(fmaf(t, t, 1.0f));
+                        sn = t * cs;
+                        ok = 1;
+                    }
+                }
+                e.rp[me] = p;
+                e.rq[me] = q;
+                e.rc[me] = cs;
+                e.rs[me] = sn;
+                e.rok[me] = ok;
+            }
+            team_sync<TEAM>();
+            for (int q = me; q < n * half; q += TEAM) {  // T <- T J
+                const int r = q % n, w = q / n;
+                if (!e.rok[w]) continue;
+                const int p = e.rp[w], qq = e.rq[w];
+                const float cs = e.rc[w], sn = e.rs[w];
+                const float a = e.Tf[r][p], b = e.Tf[r][qq];
+                e.Tf[r][p] = cs * a - sn * b;
+                e.Tf[r][qq] = sn * a + cs * b;
+            }
+            team_sync<TEAM>();
+            for (int q = me; q < n * half; q += TEAM) {  // T <- J^T T, W <- W J
+                const int r = q % n, w = q / n;
+                if (!e.rok[w]) continue;
+                const int p = e.rp[w], qq = e.rq[w];
+                const float cs = e.rc[w], sn = e.rs[w];
+                const float a = e.Tf[p][r], b = e.Tf[qq][r];
+                e.Tf[p][r] = cs * a - sn * b;
+                e.Tf[qq][r] = sn * a + cs * b;
+                const float wa = e.Wf[r][p], wb = e.Wf[r][qq];
+                e.Wf[r][p] = cs * wa - sn * wb;
+                e.Wf[r][qq] = sn * wa + cs * wb;
+            }
+            team_sync<TEAM>();
+        }
+    }
+}
+
 // Eigen-decomposition of the symmetric n x n matrix e.T (n <= NM, scaled to
 // about unit norm; e.Tf holds its FP32 copy and e.Wf the identity on entry).
-// The cyclic Jacobi method in FP32 (round-robin order) runs on warp 0; the
-// eigenvectors are then refined in double-float by the Ogita-Aishima
-// iteration for symmetric eigendecompositions (T. Ogita, K. Aishima,
-// "Iterative refinement for symmetric eigenvalue decomposition", Japan J.
-// Indust. Appl. Math. 35, 2018), whose matrix products are spread over the
-// whole block.  Leaves the eigenvectors in e.W (columns) and the eigenvalues
-// in e.lam, unsorted.  Every thread of the block calls it.
+// The cyclic Jacobi method in FP32 runs on warp 0 for orders up to 8 and on
+// the whole block above; the eigenvectors are then refined in double-float
+// by the Ogita-Aishima iteration for symmetric eigendecompositions
+// (T. Ogita, K. Aishima, "Iterative refinement for symmetric eigenvalue
+// decomposition", Japan J. Indust. Appl. Math. 35, 2018), whose matrix
+// products are spread over the whole block.  Leaves the eigenvectors in e.W
+// (columns) and the eigenvalues in e.lam, unsorted.  Every thread of the
+// block calls it.
 template <int NM>
 __device__ void sym_eig(SymEig<NM>& e, int n)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (warp == 0) {
-        const int m = n + (n & 1), half = m / 2;
-        for (int q = lane; q < (m - 1) * m; q += 32) {  // round-robin seating, one row per round
-            const int round = q / m, seat = q - (q / m) * m;
-            e.rr[round][seat] = static_cast<unsigned char>(rr_player(seat, round, m));
-        }
-        float tot = 0.0f;
-        for (int q = lane; q < n * n; q += 32) tot = fmaf(e.Tf[q / n][q % n], e.Tf[q / n][q % n], tot);
-        tot = warp_sumf(tot);
-        __syncwarp();
-        float prev = 3.0e38f;
-        for (int sweep = 0; sweep < JACOBI_SWEEPS; ++sweep) {
-            float off = 0.0f;
-            for (int q = lane; q < n * n; q += 32) {
-                const int a = q / n, b = q % n;
-                if (a != b) off = fmaf(e.Tf[a][b], e.Tf[a][b], off);
-            }
-            off = warp_sumf(off);
-            if (off <= 1e-11f * tot || off >= 0.25f * prev) break;  // converged, or stalled at FP32 rounding
-            prev = off;
-            for (int round = 0; round < m - 1; ++round) {
-                if (lane < half) {
-                    const int a = e.rr[round][lane], b = e.rr[round][m - 1 - lane];
-                    const int p = min(a, b), q = max(a, b);
-                    int ok = 0;
-                    float cs = 1.0f, sn = 0.0f;
-                    if (q < n) {
-                        const float apq = e.Tf[p][q];
-                        if (apq != 0.0f) {
-                            // approximate intrinsics suffice: the refinement below
-                            // restores accuracy, only orthogonal-enough rotations matter
-                            const float tau = __fdividef(e.Tf[q][q] - e.Tf[p][p], 2.0f * apq);
-                            float t;
-                            if (fabsf(tau) > 1e15f) t = __fdividef(0.5f, tau);
-                            else t = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.0f))), tau);
-                            cs = rsqrtf(fmaf(t, t, 1.0f));
-                            sn = t * cs;
-                            ok = 1;
-                        }
-                    }
-                    e.rp[lane] = p;
-                    e.rq[lane] = q;
-                    e.rc[lane] = cs;
-                    e.rs[lane] = sn;
-                    e.rok[lane] = ok;
-                }
-                __syncwarp();
-                for (int q = lane; q < n * half; q += 32) {  // T <- T J
-                    const int r = q % n, w = q / n;
-                    if (!e.rok[w]) continue;
-                    const int p = e.rp[w], qq = e.rq[w];
-                    const float cs = e.rc[w], sn = e.rs[w];
-                    const float a = e.Tf[r][p], b = e.Tf[r][qq];
-                    e.Tf[r][p] = cs * a - sn * b;
-                    e.Tf[r][qq] = sn * a + cs * b;
-                }
-                __syncwarp();
-                for (int q = lane; q < n * half; q += 32) {  // T <- J^T T, W <- W J
-                    const int r = q % n, w = q / n;
-                    if (!e.rok[w]) continue;
-                    const int p = e.rp[w], qq = e.rq[w];
-                    const float cs = e.rc[w], sn = e.rs[w];
-                    const float a = e.Tf[p][r], b = e.Tf[qq][r];
-                    e.Tf[p][r] = cs * a - sn * b;
-                    e.Tf[qq][r] = sn * a + cs * b;
-                    const float wa = e.Wf[r][p], wb = e.Wf[r][qq];
-                    e.Wf[r][p] = cs * wa - sn * wb;
-                    e.Wf[r][qq] = sn * wa + cs * wb;
-                }
-                __syncwarp();
-            }
-        }
+    const int tid = threadIdx.x;
+    if (n > 8) {
+        jacobi_team<NM, TPB>(e, n);
+    } else if ((tid >> 5) == 0) {
+        jacobi_team<NM, 32>(e, n);
     }
     __syncthreads();
 
