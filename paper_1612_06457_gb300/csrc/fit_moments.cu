@@ -442,44 +442,56 @@ __device__ __forceinline__ void moments_flush(DevModel* __restrict__ dm, int c, 
     }
 }
 
+// Row stride (floats) of the Gram matrix in shared memory: odd, so that the
+// strided reads below spread over the banks.
+__host__ __device__ constexpr int cs_stride(int F2) { return F2 + 1; }
+
+// Dynamic shared memory of the moment kernels for padded width F: the split
+// matrix and the Gram matrix.
+__host__ __device__ constexpr size_t moments_smem_bytes(int F)
+{
+    return static_cast<size_t>(2 * F) * UPAD * 2 + static_cast<size_t>(2 * F) * cs_stride(2 * F) * 4;
+}
+
 // The Gram matrix of a staged unit (XT: the (2 F) x 256 split matrix [h ; l]
 // in shared memory) on the tensor cores, added to the thread's moment sums.
-// Every thread of the CTA takes part (two barriers; the caller synchronizes
-// after staging).
+// A warp task is one 16-row block against two 8-column blocks, so each A
+// fragment feeds two mma (two independent accumulator chains); the Gram
+// matrix is symmetric and only entries on or above the diagonal are read, so
+// tasks wholly below it are skipped.  Every thread of the CTA takes part (two
+// barriers; the caller synchronizes after staging).
 __device__ __forceinline__ void moments_gram(const uint16_t* XT, float* Cs, int F, int npair, const unsigned char* pa,
                                              const unsigned char* pb, unsigned long long (&acc)[3])
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int F2 = 2 * F;
-    const int MT = F2 / 16, NTL = F2 / 8;
-    // one 16 x 8 output tile per warp at a time; the Gram matrix is
-    // symmetric and only entries on or above the diagonal are read, so
-    // tiles wholly below it are skipped
-    for (int t = warp; t < MT * NTL; t += NW) {
-        const int mt = t / NTL, nt = t - (t / NTL) * NTL;
-        if (nt * 8 + 7 < mt * 16) continue;
-        // two independent accumulator chains (even and odd k steps); both
-        // hold integers below 2^24, so their sum is exact as well
-        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f}, e[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int F2 = 2 * F, CS = cs_stride(F2);
+    const int MT = F2 / 16, NP = F2 / 16;  // 16-row blocks, pairs of 8-column blocks
+    for (int t = warp; t < MT * NP; t += NW) {
+        const int mt = t / NP, np = t - (t / NP) * NP;
+        if (np * 16 + 15 < mt * 16) continue;
+        // every partial sum is an integer below 2^24: exact in FP32
+        float d0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, d1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         const uint16_t* arow = XT + (mt * 16 + (lane & 15)) * UPAD + ((lane >> 4) << 3);
-        const uint16_t* brow = XT + (nt * 8 + (lane & 7)) * UPAD + (((lane >> 3) & 1) << 3);
+        const uint16_t* brow0 = XT + (np * 16 + (lane & 7)) * UPAD + (((lane >> 3) & 1) << 3);
+        const uint16_t* brow1 = brow0 + 8 * UPAD;
         #pragma unroll 4
-        for (int ks = 0; ks < UNIT / 16; ks += 2) {
-            uint32_t af[4], bfr[2], ag[4], bg[2];
+        for (int ks = 0; ks < UNIT / 16; ++ks) {
+            uint32_t af[4], b0[2], b1[2];
             ldsm_x4(af, arow + ks * 16);
-            ldsm_x2(bfr, brow + ks * 16);
-            ldsm_x4(ag, arow + ks * 16 + 16);
-            ldsm_x2(bg, brow + ks * 16 + 16);
-            mma_bf16_16816(d, af, bfr);
-            mma_bf16_16816(e, ag, bg);
+            ldsm_x2(b0, brow0 + ks * 16);
+            ldsm_x2(b1, brow1 + ks * 16);
+            mma_bf16_16816(d0, af, b0);
+            mma_bf16_16816(d1, af, b1);
         }
-        #pragma unroll
-        for (int i = 0; i < 4; ++i) d[i] = __fadd_rn(d[i], e[i]);
-        const int r0 = mt * 16 + (lane >> 2), c0 = nt * 8 + (lane & 3) * 2;
-        Cs[r0 * F2 + c0] = d[0];
-        Cs[r0 * F2 + c0 + 1] = d[1];
-        Cs[(r0 + 8) * F2 + c0] = d[2];
-        Cs[(r0 + 8) * F2 + c0 + 1] = d[3];
+        const int r0 = mt * 16 + (lane >> 2), c0 = np * 16 + (lane & 3) * 2;
+        Cs[r0 * CS + c0] = d0[0];
+        Cs[r0 * CS + c0 + 1] = d0[1];
+        Cs[(r0 + 8) * CS + c0] = d0[2];
+        Cs[(r0 + 8) * CS + c0 + 1] = d0[3];
+        Cs[r0 * CS + c0 + 8] = d1[0];
+        Cs[r0 * CS + c0 + 9] = d1[1];
+        Cs[(r0 + 8) * CS + c0 + 8] = d1[2];
+        Cs[(r0 + 8) * CS + c0 + 9] = d1[3];
     }
     __syncthreads();
     #pragma unroll
@@ -487,10 +499,10 @@ __device__ __forceinline__ void moments_gram(const uint16_t* XT, float* Cs, int 
         const int q = tid + k * TPB;
         if (q < npair) {
             const int a = pa[q], b = pb[q];
-            const unsigned long long hh = __float2uint_rn(Cs[a * F2 + b]);
-            const unsigned long long hl = __float2uint_rn(Cs[a * F2 + F + b]);
-            const unsigned long long lh = __float2uint_rn(Cs[b * F2 + F + a]);  // = C[F + a][b] by symmetry
-            const unsigned long long ll = __float2uint_rn(Cs[(F + a) * F2 + F + b]);
+            const unsigned long long hh = __float2uint_rn(Cs[a * CS + b]);
+            const unsigned long long hl = __float2uint_rn(Cs[a * CS + F + b]);
+            const unsigned long long lh = __float2uint_rn(Cs[b * CS + F + a]);  // = C[F + a][b] by symmetry
+            const unsigned long long ll = __float2uint_rn(Cs[(F + a) * CS + F + b]);
             acc[k] += (hh << 16) + ((hl + lh) << 8) + ll;
         }
     }
@@ -554,7 +566,7 @@ k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevMode
     const int nb = mom_shape(B).nb;
     const int tid = threadIdx.x;
     uint16_t* XT = reinterpret_cast<uint16_t*>(dyn);                     // F2 x UPAD bf16
-    float* Cs = reinterpret_cast<float*>(dyn + F2 * UPAD * 2);           // F2 x F2
+    float* Cs = reinterpret_cast<float*>(dyn + F2 * UPAD * 2);           // F2 x cs_stride(F2)
 
     if (tid == 0) {
         unsigned int run = 0, units = 0;
@@ -645,7 +657,7 @@ kb_moments(const PageDev* __restrict__ pages, int n, const BatchTotals* __restri
     __shared__ unsigned int s_row0;
     const int tid = threadIdx.x;
     uint16_t* XT = reinterpret_cast<uint16_t*>(dyn);                          // (2 max_f) x UPAD bf16
-    float* Cs = reinterpret_cast<float*>(dyn + 2 * max_f * UPAD * 2);         // (2 max_f)^2
+    float* Cs = reinterpret_cast<float*>(dyn + 2 * max_f * UPAD * 2);         // Gram, row stride cs_stride
 
     unsigned long long acc[3] = {0ull, 0ull, 0ull};
     int cur_page = -1, cur_class = -1, cur_b = -1;
@@ -844,7 +856,7 @@ cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const u
     if (e != cudaSuccess) return e;
 
     const int F2 = 2 * xtr_row(B);
-    const size_t smem = static_cast<size_t>(F2) * UPAD * 2 + static_cast<size_t>(F2) * F2 * 4;
+    const size_t smem = moments_smem_bytes(F2 / 2);
     e = cudaFuncSetAttribute(k_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     // the unit count is only known on the device: size the grid for the
@@ -883,7 +895,7 @@ cudaError_t launch_batch_moments(const PageDev* pages, int n, const BatchTotals*
                                  int max_b, int num_sms, cudaStream_t s)
 {
     const int F = xtr_row(max_b);
-    const size_t smem = static_cast<size_t>(2 * F) * UPAD * 2 + static_cast<size_t>(2 * F) * (2 * F) * 4;
+    const size_t smem = moments_smem_bytes(F);
     cudaError_t e = cudaFuncSetAttribute(kb_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kb_moments<<<static_cast<unsigned>(num_sms * 4), TPB, smem, s>>>(pages, n, tot, xtr_pool, F);
@@ -899,8 +911,7 @@ cudaError_t launch_pca_moments(const uint16_t* cube, int B, long long P, const u
 {
     const int vec = (P % 8 == 0) && (reinterpret_cast<uintptr_t>(cube) % 16 == 0) &&
                     (!mask || reinterpret_cast<uintptr_t>(mask) % 8 == 0);
-    const int F2 = 2 * xtr_row(B);
-    const size_t smem = static_cast<size_t>(F2) * UPAD * 2 + static_cast<size_t>(F2) * F2 * 4;
+    const size_t smem = moments_smem_bytes(xtr_row(B));
     cudaError_t e = cudaFuncSetAttribute(k_pca_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     k_pca_reset<<<1, 256, 0, s>>>(dm, B);
