@@ -37,6 +37,7 @@ namespace {
 
 using cva::BatchTotals;
 using cva::DevModel;
+using cva::device_visible;
 using cva::PageDev;
 
 constexpr int SETUP_CHUNK = 24;          // pages per set-up launch (3 KB of kernel parameters)
@@ -181,18 +182,6 @@ __global__ void kb_status(const DevModel* __restrict__ dms, int n, int* __restri
         const int st = dm->status;
         status[p] = (st == 0 && !dm->fitted) ? CVA_ERR_NOT_FITTED : st;
     }
-}
-
-bool device_visible(const void* p)
-{
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
-           (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr);
 }
 
 }  // namespace

@@ -34,24 +34,11 @@ constexpr size_t HIST_WORDS = static_cast<size_t>(cva::MAXB) * 2 * 2048;
 namespace {
 
 using cva::DevModel;
+using cva::device_visible;
 
 int from_cuda(cudaError_t e)
 {
     return e == cudaSuccess ? CVA_OK : CVA_ERR_CUDA;
-}
-
-// A pointer the GPU can read: device or managed memory, or host memory that
-// is registered / mapped.  Plain pageable host memory is refused.
-bool device_visible(const void* p)
-{
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
-           (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr);
 }
 
 bool valid_dims(int B, int H, int W)

@@ -242,6 +242,20 @@ cudaError_t launch_batch_train_range(const PageDev* pages, int n, const BatchTot
 cudaError_t launch_batch_project(const PageDev* pages, const int* item_page, long long it_begin, long long it_end,
                                  int groups_per_item, int grid, int k, cudaStream_t s);
 
+// A pointer the GPU can read: device or managed memory, or host memory that
+// is registered / mapped.  Plain pageable host memory is refused.
+inline bool device_visible(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
+           (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr);
+}
+
 // -------------------------------------------------------------------------
 // device helpers
 // -------------------------------------------------------------------------

@@ -21,6 +21,7 @@
 namespace {
 
 using cva::DevModel;
+using cva::device_visible;
 
 constexpr long long NOALLOC_MAX_PIXELS = 1LL << 26;  // H W
 constexpr long long NOALLOC_MAX_TRAIN = 1LL << 18;   // training pixels
@@ -70,17 +71,6 @@ int scratch_for_current_device(unsigned char** addr, int* sms)
     *addr = g_scratch_addr[dev];
     *sms = g_num_sms[dev];
     return CVA_OK;
-}
-
-bool device_visible(const void* p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
-           (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr);
 }
 
 }  // namespace
