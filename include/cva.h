@@ -47,8 +47,8 @@ extern "C" {
 #define CVA_ERR_INVALID_ARG (-1)    /* bad size, pointer, mode or alignment */
 #define CVA_ERR_EMPTY_CLASS (-2)    /* a class has no training pixel */
 #define CVA_ERR_NOT_SPD (-3)        /* within-class scatter not positive definite */
-#define CVA_ERR_NO_CONVERGENCE (-4) /* eigensolver hit its sweep limit */
-#define CVA_ERR_TIMEOUT (-5)        /* a bounded device-side wait gave up */
+#define CVA_ERR_NO_CONVERGENCE (-4) /* the eigenvector refinement did not converge */
+#define CVA_ERR_TIMEOUT (-5)        /* reserved: no kernel of this library waits on another */
 #define CVA_ERR_CUDA (-6)           /* a CUDA runtime call failed */
 #define CVA_ERR_LABEL_RANGE (-7)    /* a label is above K */
 #define CVA_ERR_NOT_FITTED (-8)     /* the model has not been fitted */

@@ -67,7 +67,11 @@ struct SymEig {
     int rp[NM / 2], rq[NM / 2], rok[NM / 2];
     unsigned char rr[NM][NM];
     float red[3][NWARP];
+    float last_correction;  // largest entry of the last refinement correction
 };
+
+// A refinement whose last correction is still this large did not converge.
+constexpr float REFINE_FAIL = 1e-2f;
 
 struct FinSmem {
     df A[MAXB][2 * MAXB + MAXK + 1];  // [Sw | Mb | I] during elimination
@@ -326,6 +330,7 @@ __device__ void sym_eig(SymEig<NM>& e, int n)
         __syncthreads();
         for (int q = tid; q < nn; q += TPB) e.W[q / n][q % n] = df_add(e.W[q / n][q % n], e.TW[q / n][q % n]);
         __syncthreads();
+        if (tid == 0) e.last_correction = emax;
         if (emax < 1e-6f) break;  // the next correction would be below the double-float rounding
     }
 }
@@ -564,6 +569,11 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
 
     // ---- 4. FP32 cyclic Jacobi on T, then 5. refinement ----------------------
     sym_eig<MAXK>(sm.eig, K);
+    __syncthreads();
+    if (!(sm.eig.last_correction < REFINE_FAIL)) {
+        if (tid == 0) set_status(dm, CVA_ERR_NO_CONVERGENCE);
+        return;
+    }
 
     // ---- 6. eigenvalues in descending order, whitened eigenvectors ----------
     if (tid == 0) {
@@ -759,6 +769,11 @@ __global__ void __launch_bounds__(TPB) k_pca_finalize(DevModel* __restrict__ dm,
     }
     __syncthreads();
     sym_eig<MAXB>(sm.eig, B);
+    __syncthreads();
+    if (!(sm.eig.last_correction < REFINE_FAIL)) {
+        if (tid == 0) set_status(dm, CVA_ERR_NO_CONVERGENCE);
+        return;
+    }
     if (tid == 0) {
         unsigned int used = 0u;
         for (int j = 0; j < B; ++j) {
