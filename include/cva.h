@@ -8,6 +8,15 @@
  * the three rescales) and Section 4 (the generalized symmetric-definite
  * eigenproblem solved by GSL, and the eigenvector sign ambiguity).
  *
+ * Contents: models and the fit (cva_model_*, cva_fit, cva_set_variates,
+ * cva_set_precision, getters); projections and rescales (cva_project,
+ * cva_to_u8, cva_project_u8, the third rescale's cva_percentile_range,
+ * cva_to_u16); principal components (cva_pca_fit); Section 3's evaluation
+ * indices and the colour composite (cva_cluster_indices, cva_rgb_composite);
+ * the batched form for many pages (cva_batch_*, cva_fit_project_batched,
+ * cva_project_batched); and an allocation-free fit + projection
+ * (cva_fit_project_u8_noalloc).
+ *
  * Conventions shared by every call:
  *   - Data pointers marked "device" must point to device memory of the
  *     current CUDA device; the caller owns them.  Host pointers are marked
