@@ -205,6 +205,12 @@ struct cva_batch {
     int gpi;               // pixel groups (TPB x 8 pixels) per projection item
     int grid_per_sm;       // persistent projection CTAs per SM, each on a contiguous run of items (0: one CTA per item)
     PageDev* host_pages;   // scratch for building the table
+    // side streams and events: the projection launches of the variate counts
+    // run side by side (fork from and join to the caller's stream; a
+    // captured graph records them as parallel branches)
+    cudaStream_t side[MAX_BATCH_VARIATES];
+    cudaEvent_t fork;
+    cudaEvent_t join[MAX_BATCH_VARIATES];
 };
 
 namespace {
@@ -220,6 +226,11 @@ void free_batch(cva_batch* b)
     cudaFree(b->status);
     cudaFree(b->tile_page);
     cudaFree(b->item_page);
+    for (int i = 0; i < MAX_BATCH_VARIATES; ++i) {
+        if (b->side[i]) cudaStreamDestroy(b->side[i]);
+        if (b->join[i]) cudaEventDestroy(b->join[i]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     delete[] b->host_pages;
     delete b;
 }
@@ -323,12 +334,17 @@ int projection_grid(const cva_batch* b, long long items)
 
 cudaError_t launch_projection(cva_batch* b, int n, const Plan& plan, cudaStream_t s)
 {
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaEventRecord(b->fork, s);
     for (int k = 1; k <= MAX_BATCH_VARIATES && e == cudaSuccess; ++k) {
         const long long items = plan.kend[k] - plan.kbeg[k];
-        if (items > 0)
+        if (items <= 0) continue;
+        cudaStream_t t = b->side[k - 1];
+        e = cudaStreamWaitEvent(t, b->fork, 0);
+        if (e == cudaSuccess)
             e = cva::launch_batch_project(b->pages, b->item_page, plan.kbeg[k], plan.kend[k], b->gpi,
-                                          projection_grid(b, items), k, s);
+                                          projection_grid(b, items), k, t);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join[k - 1], t);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[k - 1], 0);
     }
     // pages the batched kernel does not take (pixel count or alignment)
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
@@ -397,6 +413,11 @@ int cva_batch_create(int max_pages, int64_t max_pixels, int64_t max_train, cva_b
     ok = ok && cudaMalloc(&b->tile_page, sizeof(int) * b->tiles_cap) == cudaSuccess;
     ok = ok && cudaMalloc(&b->item_page, sizeof(int) * b->max_items) == cudaSuccess;
     ok = ok && cudaMemset(b->dms, 0, sizeof(DevModel) * max_pages) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < MAX_BATCH_VARIATES && ok; ++i) {
+        ok = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+    }
     ok = ok && cudaMemset(b->pages, 0, sizeof(PageDev) * max_pages) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
