@@ -3,8 +3,8 @@
 Argument marshalling only: every computation runs in the CUDA kernels of
 ``libcva.so``.  Functions keep the C names; where the C call takes a device
 pointer plus its sizes, the binding takes a CUDA tensor and reads the sizes
-from its shape.  A missing library raises at import time of the binding,
-never falls back to anything else.
+from its shape.  A missing library raises ImportError on first use; nothing
+ever falls back to another implementation.
 """
 from __future__ import annotations
 
