@@ -231,7 +231,8 @@ def _oracle_bands(w, seconds, steps=None):
                 raise SystemExit("no band of the page holds every class")
             rows = min(w.H, rows * 2)
     n = steps if steps is not None else max(3, int(seconds / max(t * 4, 1e-6)))
-    rows = int(max(rows, min(w.H, rows * (seconds / n) / max(t, 1e-6))))
+    # the band may shrink below the first one; a band that misses a class is widened below
+    rows = int(max(32, min(w.H, rows * (seconds / n) / max(t, 1e-6))))
     times = []
     for i in range(n):
         band = rows
