@@ -371,3 +371,55 @@ def test_output_only_4_byte_aligned():
     cva.cva_project_u8(cube, m, 2, cva.CVA_RANGE_TRAINING, o2)
     assert torch.equal(o1, o2)
     m.close()
+
+
+def test_full_16_bit_values():
+    """Values over the whole uint16 range (up to 65535): the exact moments
+    (products up to 2^32, byte split still exact in bf16) and the exact FP32
+    centring hold at the top of the range."""
+    _skip_without_gpu()
+    w = make_workload(116, 23, 200, 256, 4, (3000, 2000, 1500, 900), 3, separation=(1.0, 4.0), both=True)
+    c = w.cube.astype(np.uint64)
+    c16 = (c * 65535 // c.max()).astype(np.uint16)
+    assert c16.max() == 65535
+    w.cube = c16
+    ref = oracle.fit(w.cube, w.labels, w.K)
+    m, cube, labels, g = _gpu_fit(w, nvec=3)
+    _check_fit(g, ref, w.K, w.B, 3)
+    out = torch.empty((3, w.H, w.W), dtype=torch.uint8, device=DEV)
+    cva.cva_project_u8(cube, m, 3, cva.CVA_RANGE_TRAINING, out)
+    y_ref = oracle.project(w.cube, ref["V"], ref["mu"], 3)
+    u_ref = oracle.to_u8(y_ref, oracle.range_training(y_ref, w.labels))
+    assert _u8_ok(out.cpu().numpy().reshape(3, -1), u_ref) >= 0.999
+    y = torch.empty((3, w.H, w.W), dtype=torch.float32, device=DEV)
+    cva.cva_project(cube, m, 3, out_f32=y)
+    assert _normwise(y.cpu().numpy().reshape(3, -1), y_ref) <= 1e-4
+    m.close()
+
+
+def test_single_page_step_in_a_cuda_graph():
+    """Fit + fused projection captured once and replayed (as the benchmark
+    runs it) give the eager results; the library allocates nothing in
+    either call, so the capture holds."""
+    _skip_without_gpu()
+    w = make_workload(117, 16, 256, 320, 3, (2000, 1500, 1200), 2, separation=(1.0, 4.0), both=False)
+    m, cube, labels, g = _gpu_fit(w, nvec=2)
+    eager = torch.empty((2, w.H, w.W), dtype=torch.uint8, device=DEV)
+    cva.cva_project_u8(cube, m, 2, cva.CVA_RANGE_TRAINING, eager)
+    s = torch.cuda.Stream()
+    out = torch.empty_like(eager)
+    with torch.cuda.stream(s):
+        cva.cva_fit(cube, labels, w.K, m, stream=s)
+        cva.cva_project_u8(cube, m, 2, cva.CVA_RANGE_TRAINING, out, stream=s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        cva.cva_fit(cube, labels, w.K, m, stream=s)
+        cva.cva_project_u8(cube, m, 2, cva.CVA_RANGE_TRAINING, out, stream=s)
+    out.zero_()
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert cva.cva_status(m) == cva.CVA_OK
+    assert torch.equal(out, eager)
+    m.close()
