@@ -209,7 +209,10 @@ __device__ void jacobi_team(SymEig<NM>& e, int n)
                         const float tau = __fdividef(e.Tf[q][q] - e.Tf[p][p], 2.0f * apq);
                         float t;
                         if (fabsf(tau) > 1e15f) t = __fdividef(0.5f, tau);
-                        else t = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.0f))), tau);
+                        else {
+                            const float q = fmaf(tau, tau, 1.0f);  // >= 1: q rsqrt(q) is sqrt(q)
+                            t = copysignf(__fdividef(1.0f, fabsf(tau) + q * rsqrtf(q)), tau);
+                        }
                         cs = rsqrtf(fmaf(t, t, 1.0f));
                         sn = t * cs;
                         ok = 1;
