@@ -337,6 +337,16 @@ def _precision_forms(cva, torch, w, m, cube, labels, out, stream, steps=5):
     return res
 
 
+def _extra(fn, *args, **kw):
+    """Run one of the line's extra measurements; a failure is reported in the
+    line as ``{"error": ...}`` instead of ending the run, so the headline keys
+    (value, roofline, e2e, clocks) are always printed."""
+    try:
+        return fn(*args, **kw)
+    except Exception as exc:  # noqa: BLE001 - any failure of an extra is recorded
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
 def _time_calls(torch, fn, stream, reps=20):
     with torch.cuda.stream(stream):
         for _ in range(3):
@@ -621,10 +631,13 @@ def run_ours(a):
 
     precision = None
     if rank == 0 and not a.no_precision:
-        precision = _precision_forms(cva, torch, w, m, cube, labels, out, stream)
-    others = _other_outputs(cva, torch, w, m, cube, stream, _peaks()[0]) if rank == 0 and not a.no_precision else None
-    if others is not None:
-        others["page_stream"] = _page_stream(cva, torch, w, cube, labels, out, stream, max(20, min(a.steps, 200)))
+        precision = _extra(_precision_forms, cva, torch, w, m, cube, labels, out, stream)
+        cva.cva_set_precision(m, cva.CVA_PRECISION_MIXED)
+    others = None
+    if rank == 0 and not a.no_precision:
+        others = _extra(_other_outputs, cva, torch, w, m, cube, stream, _peaks()[0])
+        others["page_stream"] = _extra(_page_stream, cva, torch, w, cube, labels, out, stream,
+                                       max(20, min(a.steps, 200)))
 
     if rank == 0:
         peak, peak_kind = _peaks()
@@ -657,16 +670,19 @@ def run_ours(a):
         if not a.no_cpu_baseline and world == 1:
             rows = max(1, min(w.H, 256 * 4096 // max(w.W, 1)))
             keep = {}
-            _oracle_step_time(w, rows, keep)
-            errs = _errors_vs_oracle(cva, torch, w, m, cube, out, keep, stream)
+            errs = _extra(lambda: (_oracle_step_time(w, rows, keep),
+                                   _errors_vs_oracle(cva, torch, w, m, cube, out, keep, stream))[1])
             if precision is not None:
                 precision["err_vs_oracle"] = errs
-            t, band, nb = _oracle_bands(w, CPU_BASELINE_S)
-            line["cpu_baseline"] = {
-                "value": P / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": (f"median of {nb} runs of the oracle on a band of {band} of {w.H} rows taken as a page "
-                           f"(fit, training range, projection, 8-bit rescale), about {CPU_BASELINE_S:.0f} s in all, "
-                           f"time scaled to the full page")}
+            try:
+                t, band, nb = _oracle_bands(w, CPU_BASELINE_S)
+                line["cpu_baseline"] = {
+                    "value": P / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": (f"median of {nb} runs of the oracle on a band of {band} of {w.H} rows taken as a "
+                               f"page (fit, training range, projection, 8-bit rescale), about "
+                               f"{CPU_BASELINE_S:.0f} s in all, time scaled to the full page")}
+            except Exception as exc:  # noqa: BLE001 - reported in the line
+                line["cpu_baseline"] = {"error": f"{type(exc).__name__}: {exc}", "kind": "oracle"}
         print(json.dumps(line), flush=True)
     m.close()
     if dist is not None:
