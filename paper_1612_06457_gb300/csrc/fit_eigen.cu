@@ -19,12 +19,13 @@
 //       Mb[:, c] = sqrt(n_c) (mu_c - mu),  mu_c - mu = (N s_c - n_c S) / (n_c N)
 //     again from exact numerators, so that Sb = Mb Mb^T;
 //  2. right-looking Cholesky Sw = L L^T with Mb carried along as extra
-//     columns, giving G = L^-1 Mb in the same elimination (two barriers per
-//     column; the next pivot's reciprocal square root is taken by the thread
-//     that finishes that diagonal entry);
+//     columns, giving G = L^-1 Mb in the same elimination (one barrier per
+//     column; warp 0 alone updates the next pivot and takes its reciprocal
+//     square root, the critical path of the elimination);
 //  3. L^-1 Sb L^-T = G G^T has rank <= K - 1 and the same non-zero
 //     eigenvalues as the K x K matrix T = G^T G.  T is diagonalized by the
-//     cyclic Jacobi method in FP32 (round-robin order, one warp), and the
+//     cyclic Jacobi method in FP32 (one thread, in registers, up to order 8;
+//     round-robin order over the block above), and the
 //     eigenvectors are then refined in double-float by two steps of the Ogita-Aishima
 //     iteration for symmetric eigendecompositions (T. Ogita, K. Aishima,
 //     "Iterative refinement for symmetric eigenvalue decomposition", Japan J.
@@ -45,10 +46,10 @@ namespace cva {
 
 namespace {
 
-constexpr int TPB = 256;
+constexpr int TPB = 384;  // 12 warps: one column of the elimination fits one pass from column 5 on
 constexpr int NWARP = TPB / 32;
 constexpr int JACOBI_SWEEPS = 40;
-constexpr int REFINE_STEPS = 3;
+constexpr int REFINE_STEPS = 6;
 constexpr int MAXTRI = MAXB * (MAXB + 1) / 2;
 
 // Work space of the symmetric eigensolver for matrices of order <= NM.
@@ -169,9 +170,9 @@ __device__ inline void team_sync()
 }
 
 // Cyclic Jacobi on e.Tf (round-robin order) in FP32, accumulating the
-// rotations in e.Wf.  Run by warp 0 alone for small orders (TEAM = 32) or by
-// the whole block (TEAM = TPB), which applies the rotations of a round in
-// parallel over all its threads.
+// rotations in e.Wf.  Run by the whole block (TEAM = TPB), which applies the
+// rotations of a round in parallel over all its threads, for orders above 8
+// (jacobi_serial takes the smaller ones); TEAM = 32 runs it on warp 0 alone.
 template <int NM, int TEAM>
 __device__ void jacobi_team(SymEig<NM>& e, int n)
 {
@@ -193,7 +194,10 @@ __device__ void jacobi_team(SymEig<NM>& e, int n)
             if (a != b) off = fmaf(e.Tf[a][b], e.Tf[a][b], off);
         }
         off = team_sumf<NM, TEAM>(e, off);
-        if (off <= 1e-11f * tot || off >= 0.25f * prev) break;  // converged, or stalled at FP32 rounding
+        // converged, or stalled at FP32 rounding; the stall is only judged once
+        // the off-diagonal part is small, as an early sweep may shrink it by
+        // less than a factor of 4
+        if (off <= 1e-11f * tot || (off >= 0.25f * prev && off <= 1e-9f * tot)) break;
         prev = off;
         for (int round = 0; round < m - 1; ++round) {
             if (me < half) {
@@ -252,9 +256,80 @@ __device__ void jacobi_team(SymEig<NM>& e, int n)
     }
 }
 
+// The same cyclic Jacobi method for orders N <= 8 on one thread, with the
+// matrix and the accumulated rotations in registers and the rotations taken
+// in row-cyclic order: at these orders a warp spends most of each round on
+// shared-memory round trips and warp barriers, which a single thread avoids.
+template <int N, int NM>
+__device__ void jacobi_serial(SymEig<NM>& e)
+{
+    float a[N][N], w[N][N];
+    float tot = 0.0f;
+    #pragma unroll
+    for (int i = 0; i < N; ++i)
+        #pragma unroll
+        for (int j = 0; j < N; ++j) {
+            a[i][j] = e.Tf[i][j];
+            w[i][j] = (i == j) ? 1.0f : 0.0f;
+            tot = fmaf(a[i][j], a[i][j], tot);
+        }
+    float prev = 3.0e38f;
+    #pragma unroll 1
+    for (int sweep = 0; sweep < JACOBI_SWEEPS; ++sweep) {
+        float off = 0.0f;
+        #pragma unroll
+        for (int i = 0; i < N; ++i)
+            #pragma unroll
+            for (int j = 0; j < N; ++j)
+                if (i != j) off = fmaf(a[i][j], a[i][j], off);
+        // converged, or stalled at FP32 rounding (judged as in jacobi_team)
+        if (off <= 1e-11f * tot || (off >= 0.25f * prev && off <= 1e-9f * tot)) break;
+        prev = off;
+        #pragma unroll
+        for (int p = 0; p < N - 1; ++p)
+            #pragma unroll
+            for (int q = p + 1; q < N; ++q) {
+                const float apq = a[p][q];
+                if (apq == 0.0f) continue;
+                // approximate intrinsics suffice: the refinement restores accuracy
+                const float tau = __fdividef(a[q][q] - a[p][p], 2.0f * apq);
+                float t;
+                if (fabsf(tau) > 1e15f) t = __fdividef(0.5f, tau);
+                else {
+                    const float u = fmaf(tau, tau, 1.0f);  // >= 1: u rsqrt(u) is sqrt(u)
+                    t = copysignf(__fdividef(1.0f, fabsf(tau) + u * rsqrtf(u)), tau);
+                }
+                const float cs = rsqrtf(fmaf(t, t, 1.0f));
+                const float sn = t * cs;
+                #pragma unroll
+                for (int k = 0; k < N; ++k) {  // A <- A J
+                    const float x = a[k][p], y = a[k][q];
+                    a[k][p] = cs * x - sn * y;
+                    a[k][q] = sn * x + cs * y;
+                }
+                #pragma unroll
+                for (int k = 0; k < N; ++k) {  // A <- J^T A, W <- W J
+                    const float x = a[p][k], y = a[q][k];
+                    a[p][k] = cs * x - sn * y;
+                    a[q][k] = sn * x + cs * y;
+                    const float wx = w[k][p], wy = w[k][q];
+                    w[k][p] = cs * wx - sn * wy;
+                    w[k][q] = sn * wx + cs * wy;
+                }
+            }
+    }
+    #pragma unroll
+    for (int i = 0; i < N; ++i)
+        #pragma unroll
+        for (int j = 0; j < N; ++j) {
+            e.Tf[i][j] = a[i][j];
+            e.Wf[i][j] = w[i][j];
+        }
+}
+
 // Eigen-decomposition of the symmetric n x n matrix e.T (n <= NM, scaled to
 // about unit norm; e.Tf holds its FP32 copy and e.Wf the identity on entry).
-// The cyclic Jacobi method in FP32 runs on warp 0 for orders up to 8 and on
+// The cyclic Jacobi method in FP32 runs on thread 0 for orders up to 8 and on
 // the whole block above; the eigenvectors are then refined in double-float
 // by the Ogita-Aishima iteration for symmetric eigendecompositions
 // (T. Ogita, K. Aishima, "Iterative refinement for symmetric eigenvalue
@@ -268,8 +343,17 @@ __device__ void sym_eig(SymEig<NM>& e, int n)
     const int tid = threadIdx.x;
     if (n > 8) {
         jacobi_team<NM, TPB>(e, n);
-    } else if ((tid >> 5) == 0) {
-        jacobi_team<NM, 32>(e, n);
+    } else if (tid == 0) {
+        switch (n) {
+            case 1: jacobi_serial<1>(e); break;
+            case 2: jacobi_serial<2>(e); break;
+            case 3: jacobi_serial<3>(e); break;
+            case 4: jacobi_serial<4>(e); break;
+            case 5: jacobi_serial<5>(e); break;
+            case 6: jacobi_serial<6>(e); break;
+            case 7: jacobi_serial<7>(e); break;
+            default: jacobi_serial<8>(e); break;
+        }
     }
     __syncthreads();
 
@@ -281,6 +365,7 @@ __device__ void sym_eig(SymEig<NM>& e, int n)
         for (int q = tid; q < nn; q += TPB) {
             const int a = q / n, b = q % n;
             df r = df_from(0.0f), tw = df_from(0.0f);
+            #pragma unroll 1
             for (int k = 0; k < n; ++k) {
                 r = df_fma(r, e.W[k][a], e.W[k][b]);     // W^T W
                 tw = df_fma(tw, e.T[a][k], e.W[k][b]);   // T W
@@ -293,6 +378,7 @@ __device__ void sym_eig(SymEig<NM>& e, int n)
         for (int q = tid; q < nn; q += TPB) {
             const int a = q / n, b = q % n;
             df sv = df_from(0.0f);
+            #pragma unroll 1
             for (int k = 0; k < n; ++k) sv = df_fma(sv, e.W[k][a], e.TW[k][b]);  // W^T T W
             e.S[a][b] = sv;
             if (a != b) so = fmaxf(so, fabsf(sv.hi));
@@ -327,6 +413,7 @@ __device__ void sym_eig(SymEig<NM>& e, int n)
         for (int q = tid; q < nn; q += TPB) {
             const int a = q / n, b = q % n;
             df d = df_from(0.0f);
+            #pragma unroll 1
             for (int k = 0; k < n; ++k) d = df_fma(d, e.W[a][k], e.E[k][b]);  // W E
             e.TW[a][b] = d;
         }
@@ -347,6 +434,7 @@ __device__ void complete_basis(FinSmem& sm, int B, int j0, int j1)
     for (int j = j0; j < j1; ++j) {
         if (tid < B) {
             float s = 0.0f;
+            #pragma unroll 1
             for (int l = 0; l < j; ++l) s = fmaf(sm.U[tid][l].hi, sm.U[tid][l].hi, s);
             sm.res[tid] = 1.0f - s;
         }
@@ -361,18 +449,21 @@ __device__ void complete_basis(FinSmem& sm, int B, int j0, int j1)
         const int piv = sm.pivot;
         if (tid < B) {
             df s = df_from((tid == piv) ? 1.0f : 0.0f);
+            #pragma unroll 1
             for (int l = 0; l < j; ++l) s = df_fms(s, sm.U[piv][l], sm.U[tid][l]);
             sm.q[tid] = s;
         }
         __syncthreads();
         if (tid < j) {
             df s = df_from(0.0f);
+            #pragma unroll 1
             for (int b = 0; b < B; ++b) s = df_fma(s, sm.U[b][tid], sm.q[b]);
             sm.cvec[tid] = s;
         }
         __syncthreads();
         if (tid < B) {
             df s = sm.q[tid];
+            #pragma unroll 1
             for (int l = 0; l < j; ++l) s = df_fms(s, sm.cvec[l], sm.U[tid][l]);
             sm.q[tid] = s;
         }
@@ -399,6 +490,7 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
     if (tid < K) sm.n[tid] = mom_get(dm, sh, tid, B, B);
     if (tid < B) {
         unsigned long long t = 0;
+        #pragma unroll 1
         for (int c = 0; c < K; ++c) t += mom_get(dm, sh, c, tid, B);
         sm.tot[tid] = t;
     }
@@ -412,6 +504,7 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
     if (tid == 0) {
         unsigned long long N = 0;
         int fail = 0;
+        #pragma unroll 1
         for (int c = 0; c < K; ++c) {
             N += sm.n[c];
             if (sm.n[c] == 0) fail = CVA_ERR_EMPTY_CLASS;
@@ -449,6 +542,7 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
     for (int q = tid; q < B * (B + 1) / 2; q += TPB) {
         const int i = sm.tri_i[q], l = sm.tri_l[q];
         df acc = df_from(0.0f);
+        #pragma unroll 1
         for (int c = 0; c < K; ++c) {
             const __int128 num = static_cast<__int128>(sm.n[c]) * mom_get(dm, sh, c, i, l) -
                                  static_cast<__int128>(mom_get(dm, sh, c, i, B)) * mom_get(dm, sh, c, l, B);
@@ -488,25 +582,34 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
         __syncthreads();
         if (sm.fail) break;
         // column j of L, row j of [G | L^-1], and the trailing update, in one
-        // phase: L[i][j] = A[i][j] r and the row-j entries are formed where used
+        // phase: L[i][j] = A[i][j] r and the row-j entries are formed where used.
+        // Item 0 (the next pivot, on the critical path of the elimination) is
+        // warp 0's alone, so that no warp runs both paths; the other items are
+        // spread over warps 1 .. NWARP-1.
         const df r = sm.invd[j];
         const int m = B - j - 1;
         const int ntri = m * (m + 1) / 2;
         const int ncar = j + 1 + K;  // carried columns with nonzero row j: Mb and identity columns 0..j
-        for (int e = tid; e < ntri + m * ncar + m + ncar; e += TPB) {
+        if (warp == 0) {
+            if (lane == 0 && m > 0) {  // the next pivot is final after this update: take its reciprocal square root now
+                const df a = sm.A[j + 1][j];
+                const df v = df_fms(sm.A[j + 1][j + 1], df_mul(a, r), df_mul(a, r));
+                sm.A[j + 1][j + 1] = v;
+                if (!(v.hi > static_cast<float>(PIVOT_REL) * sm.swd[j + 1]) || !(v.hi > 0.0f)) {
+                    sm.fail = CVA_ERR_NOT_SPD;
+                } else {
+                    const df rr = df_rsqrt(v);
+                    sm.invd[j + 1] = rr;
+                    sm.L[j + 1][j + 1] = df_mul(v, rr);
+                }
+            }
+            continue;
+        }
+        // item 0 is the pivot's while there is one (m > 0); in the last column it is G[j][0]
+        for (int e = tid - 32 + (m > 0 ? 1 : 0); e < ntri + m * ncar + m + ncar; e += TPB - 32) {
             if (e < ntri) {
                 const int i = j + 1 + sm.tri_i[e], l = j + 1 + sm.tri_l[e];
-                const df v = df_fms(sm.A[i][l], df_mul(sm.A[i][j], r), df_mul(sm.A[l][j], r));
-                sm.A[i][l] = v;
-                if (e == 0) {  // the next pivot is final: take its reciprocal square root now
-                    if (!(v.hi > static_cast<float>(PIVOT_REL) * sm.swd[j + 1]) || !(v.hi > 0.0f)) {
-                        sm.fail = CVA_ERR_NOT_SPD;
-                    } else {
-                        const df rr = df_rsqrt(v);
-                        sm.invd[j + 1] = rr;
-                        sm.L[j + 1][j + 1] = df_mul(v, rr);
-                    }
-                }
+                sm.A[i][l] = df_fms(sm.A[i][l], df_mul(sm.A[i][j], r), df_mul(sm.A[l][j], r));
             } else if (e < ntri + m * ncar) {
                 const int q = e - ntri;
                 const int i = j + 1 + q / ncar, cc = q - (q / ncar) * ncar;
@@ -607,6 +710,7 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
         const int b = e / rr, j = e - (e / rr) * rr;
         const int w = sm.order[j];
         df s = df_from(0.0f);
+        #pragma unroll 1
         for (int c = 0; c < K; ++c) s = df_fma(s, sm.G[b][c], sm.eig.W[c][w]);
         sm.U[b][j] = df_mul(s, df_rsqrt(sm.lam[j]));
     }
@@ -855,6 +959,7 @@ __global__ void k_scatter_sb(DevModel* __restrict__ dm, int B, int K)
     for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
         const int i = e / B, j = e % B;
         double s = 0.0;
+        #pragma unroll 1
         for (int c = 0; c < K; ++c) s = fma(dm->Mb[i][c], dm->Mb[j][c], s);
         dm->Sb[i][j] = s;
     }
