@@ -605,25 +605,40 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
             }
             continue;
         }
-        // item 0 is the pivot's while there is one (m > 0); in the last column it is G[j][0]
-        for (int e = tid - 32 + (m > 0 ? 1 : 0); e < ntri + m * ncar + m + ncar; e += TPB - 32) {
-            if (e < ntri) {
+        // item 0 is the pivot's while there is one (m > 0); in the last column it is G[j][0].
+        // Every item is X - (Y r)(Z r) (trailing and carried entries) or Y r (column j
+        // of L, row j of [G | L^-1]); only the operand addresses depend on the kind,
+        // so a warp whose items straddle two kinds diverges only while loading.
+        const float rnc = __frcp_rn(static_cast<float>(ncar));  // (q + 1/2) rnc truncates to q / ncar exactly
+        const int n1 = ntri, n2 = ntri + m * ncar, n3 = n2 + m;
+        for (int e = tid - 32 + (m > 0 ? 1 : 0); e < n3 + ncar; e += TPB - 32) {
+            df X = df_from(0.0f), Y, Z = df_from(0.0f);
+            df* dst;
+            bool fms = true;
+            if (e < n1) {
                 const int i = j + 1 + sm.tri_i[e], l = j + 1 + sm.tri_l[e];
-                sm.A[i][l] = df_fms(sm.A[i][l], df_mul(sm.A[i][j], r), df_mul(sm.A[l][j], r));
-            } else if (e < ntri + m * ncar) {
-                const int q = e - ntri;
-                const int i = j + 1 + q / ncar, cc = q - (q / ncar) * ncar;
-                const int col = B + cc;  // Mb columns, then identity columns 0..j
-                sm.A[i][col] = df_fms(sm.A[i][col], df_mul(sm.A[i][j], r), df_mul(sm.A[j][col], r));
-            } else if (e < ntri + m * ncar + m) {
-                const int i = j + 1 + (e - ntri - m * ncar);
-                sm.L[i][j] = df_mul(sm.A[i][j], r);
+                X = sm.A[i][l]; Y = sm.A[i][j]; Z = sm.A[l][j];
+                dst = &sm.A[i][l];
+            } else if (e < n2) {
+                const int q = e - n1;
+                const int qi = static_cast<int>((static_cast<float>(q) + 0.5f) * rnc);
+                const int i = j + 1 + qi, col = B + (q - qi * ncar);  // Mb columns, then identity columns 0..j
+                X = sm.A[i][col]; Y = sm.A[i][j]; Z = sm.A[j][col];
+                dst = &sm.A[i][col];
+            } else if (e < n3) {
+                const int i = j + 1 + (e - n2);
+                Y = sm.A[i][j];
+                dst = &sm.L[i][j];
+                fms = false;
             } else {
-                const int cc = e - ntri - m * ncar - m;
-                const df v = df_mul(sm.A[j][B + cc], r);
-                if (cc < K) sm.G[j][cc] = v;
-                else sm.Li[j][cc - K] = v;
+                const int cc = e - n3;
+                Y = sm.A[j][B + cc];
+                dst = (cc < K) ? &sm.G[j][cc] : &sm.Li[j][cc - K];
+                fms = false;
             }
+            const df yr = df_mul(Y, r);
+            const df v = df_fms(X, yr, df_mul(Z, r));
+            *dst = fms ? v : yr;
         }
     }
     (void)KB;
