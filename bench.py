@@ -215,6 +215,7 @@ def _oracle_band_time(w, r0, rows):
 
 
 CPU_BASELINE_S = 12.0  # CPU work of the oracle baseline beside the GPU line
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e nominal bandwidth, reported beside the measured peak
 
 
 def _oracle_bands(w, seconds, steps=None):
@@ -656,7 +657,8 @@ def run_ours(a):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": "k_project_v8 (fused projection + u8)",
                          "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
-                         "launch_ms": proj_ms},
+                         "launch_ms": proj_ms, "nominal_peak": HBM_NOMINAL_GBS,
+                         "frac_of_nominal": achieved / HBM_NOMINAL_GBS},
             "e2e": {"value": _job_value(world, P, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": int(w.cube.nbytes + w.labels.nbytes),
                     "d2h_bytes_per_step": int(out_h[0].numel()), "ms_per_step": e2e_ms, "steps": e2e_steps,
@@ -849,7 +851,8 @@ def run_batch_bench(a):
         "dtype": "f32", "data": "synthetic", "config": _batch_config(ws),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "kb_project_v8 (batched fused projection + u8)",
-                     "peak_kind": peak_kind, "alg_bytes_per_launch": alg, "launch_ms": proj_ms},
+                     "peak_kind": peak_kind, "alg_bytes_per_launch": alg, "launch_ms": proj_ms,
+                     "nominal_peak": HBM_NOMINAL_GBS, "frac_of_nominal": achieved / HBM_NOMINAL_GBS},
         "e2e": {"value": P / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(w.cube.nbytes + w.labels.nbytes for w in ws)),
                 "d2h_bytes_per_step": int(sum(o.numel() for o in outs_h)), "ms_per_step": e2e_ms,
