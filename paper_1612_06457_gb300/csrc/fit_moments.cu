@@ -551,7 +551,7 @@ __device__ __forceinline__ void moments_unit(uint16_t* XT, float* Cs, const uint
 // is recombined in 64-bit integers.  Each thread owns up to three (a <= b)
 // entries of the augmented moment matrix and keeps them in registers while
 // the CTA stays on one class.
-__global__ void __launch_bounds__(TPB)
+__global__ void __launch_bounds__(TPB, 6)
 k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevModel* __restrict__ dm)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -860,8 +860,11 @@ cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const u
     e = cudaFuncSetAttribute(k_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     // the unit count is only known on the device: size the grid for the
-    // useful maximum and let idle CTAs exit at once
-    const long long g3 = static_cast<long long>(num_sms) * 4;
+    // useful maximum and let idle CTAs exit at once.  Six CTAs an SM (40
+    // registers, ~36 KB of shared memory each) are resident together, so up
+    // to 6 x SMs units (912 on 152 SMs; 784 on the 23-band benchmark page)
+    // each take one CTA instead of two rounds
+    const long long g3 = static_cast<long long>(num_sms) * 6;
     k_moments<<<static_cast<unsigned>(g3), TPB, smem, s>>>(B, K, xtr, cap, dm);
     return cudaGetLastError();
 }
