@@ -25,9 +25,9 @@
 //  3. L^-1 Sb L^-T = G G^T has rank <= K - 1 and the same non-zero
 //     eigenvalues as the K x K matrix T = G^T G.  T is diagonalized by the
 //     cyclic Jacobi method in FP32 (one thread, in registers, up to order 8;
-//     round-robin order over the block above), and the
-//     eigenvectors are then refined in double-float by two steps of the Ogita-Aishima
-//     iteration for symmetric eigendecompositions (T. Ogita, K. Aishima,
+//     round-robin order over the block above), and the eigenvectors are then
+//     refined in double-float by the Ogita-Aishima iteration (usually one or
+//     two steps, at most REFINE_STEPS) for symmetric eigendecompositions (T. Ogita, K. Aishima,
 //     "Iterative refinement for symmetric eigenvalue decomposition", Japan J.
 //     Indust. Appl. Math. 35, 2018), which restores full accuracy from the
 //     FP32 start and tolerates its loss of orthogonality;
