@@ -24,8 +24,9 @@
 //     square root, the critical path of the elimination);
 //  3. L^-1 Sb L^-T = G G^T has rank <= K - 1 and the same non-zero
 //     eigenvalues as the K x K matrix T = G^T G.  T is diagonalized by the
-//     cyclic Jacobi method in FP32 (one thread, in registers, up to order 8;
-//     round-robin order over the block above), and the eigenvectors are then
+//     cyclic Jacobi method in FP32 (one thread, in registers, up to order 4;
+//     round-robin order on one warp up to order 8 and over the block above),
+//     and the eigenvectors are then
 //     refined in double-float by the Ogita-Aishima iteration (usually one or
 //     two steps, at most REFINE_STEPS) for symmetric eigendecompositions (T. Ogita, K. Aishima,
 //     "Iterative refinement for symmetric eigenvalue decomposition", Japan J.
@@ -170,9 +171,9 @@ __device__ inline void team_sync()
 }
 
 // Cyclic Jacobi on e.Tf (round-robin order) in FP32, accumulating the
-// rotations in e.Wf.  Run by the whole block (TEAM = TPB), which applies the
-// rotations of a round in parallel over all its threads, for orders above 8
-// (jacobi_serial takes the smaller ones); TEAM = 32 runs it on warp 0 alone.
+// rotations in e.Wf.  Run by warp 0 alone (TEAM = 32) for orders 5 to 8 or by
+// the whole block (TEAM = TPB) above, which applies the rotations of a round
+// in parallel over all its threads; jacobi_serial takes orders up to 4.
 template <int NM, int TEAM>
 __device__ void jacobi_team(SymEig<NM>& e, int n)
 {
@@ -256,10 +257,13 @@ __device__ void jacobi_team(SymEig<NM>& e, int n)
     }
 }
 
-// The same cyclic Jacobi method for orders N <= 8 on one thread, with the
+// The same cyclic Jacobi method for orders N <= 4 on one thread, with the
 // matrix and the accumulated rotations in registers and the rotations taken
 // in row-cyclic order: at these orders a warp spends most of each round on
 // shared-memory round trips and warp barriers, which a single thread avoids.
+// Orders up to 4 keep the kernel at 56 registers (two CTAs an SM for the
+// batched form, as its shared memory allows); orders 5 to 8 in registers
+// took 156.
 template <int N, int NM>
 __device__ void jacobi_serial(SymEig<NM>& e)
 {
@@ -329,12 +333,12 @@ __device__ void jacobi_serial(SymEig<NM>& e)
 
 // Eigen-decomposition of the symmetric n x n matrix e.T (n <= NM, scaled to
 // about unit norm; e.Tf holds its FP32 copy and e.Wf the identity on entry).
-// The cyclic Jacobi method in FP32 runs on thread 0 for orders up to 8 and on
-// the whole block above; the eigenvectors are then refined in double-float
-// by the Ogita-Aishima iteration for symmetric eigendecompositions
-// (T. Ogita, K. Aishima, "Iterative refinement for symmetric eigenvalue
-// decomposition", Japan J. Indust. Appl. Math. 35, 2018), whose matrix
-// products are spread over the whole block.  Leaves the eigenvectors in e.W
+// The cyclic Jacobi method in FP32 runs on thread 0 for orders up to 4, on
+// warp 0 up to 8 and on the whole block above; the eigenvectors are then
+// refined in double-float by the Ogita-Aishima iteration for symmetric
+// eigendecompositions (T. Ogita, K. Aishima, "Iterative refinement for
+// symmetric eigenvalue decomposition", Japan J. Indust. Appl. Math. 35, 2018),
+// whose matrix products are spread over the whole block.  Leaves the eigenvectors in e.W
 // (columns) and the eigenvalues in e.lam, unsorted.  Every thread of the
 // block calls it.
 template <int NM>
@@ -343,16 +347,14 @@ __device__ void sym_eig(SymEig<NM>& e, int n)
     const int tid = threadIdx.x;
     if (n > 8) {
         jacobi_team<NM, TPB>(e, n);
+    } else if (n > 4) {
+        if ((tid >> 5) == 0) jacobi_team<NM, 32>(e, n);
     } else if (tid == 0) {
         switch (n) {
             case 1: jacobi_serial<1>(e); break;
             case 2: jacobi_serial<2>(e); break;
             case 3: jacobi_serial<3>(e); break;
-            case 4: jacobi_serial<4>(e); break;
-            case 5: jacobi_serial<5>(e); break;
-            case 6: jacobi_serial<6>(e); break;
-            case 7: jacobi_serial<7>(e); break;
-            default: jacobi_serial<8>(e); break;
+            default: jacobi_serial<4>(e); break;
         }
     }
     __syncthreads();
