@@ -24,3 +24,15 @@ def test_reference_line_on_the_small_cube():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"] == "cube16b_512x512_K3"
+
+
+def test_a_failing_extra_measurement_is_reported_not_raised():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    def boom(x):
+        raise RuntimeError(f"extra failed on {x}")
+
+    r = bench._extra(boom, 3)
+    assert r == {"error": "RuntimeError: extra failed on 3"}
+    assert bench._extra(lambda a, b=2: a * b, 5, b=4) == 20
