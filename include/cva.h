@@ -292,7 +292,10 @@ int cva_project_u8(const uint16_t* cube, int B, int H, int W, cva_model* m, int 
  * 2^18 training pixels (device check, CVA_ERR_CAPACITY in *status).
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array: calls that
+ * before any stream capture.  The address is kept for the life of the
+ * process: do not call this entry point on a device after cudaDeviceReset
+ * (or any other teardown of its primary context), since the kept address no
+ * longer names the array then.  Every call shares the one array: calls that
  * overlap on the GPU (other streams, other host threads) race.  Calls are
  * asynchronous on `stream`. */
 int cva_fit_project_u8_noalloc(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, int K,
@@ -352,9 +355,9 @@ int cva_project_batched(cva_batch* b, const cva_page* pages, int n, void* stream
 int cva_batch_status(cva_batch* b, int n, int* status, void* stream);
 
 /* Autotuner of the batched projection: runs the batch once, then times the
- * projection pass with each work-item size (1, 2, 4 or 8 groups of 2048
- * pixels) and grid (two persistent CTAs per SM, each on a contiguous run of
- * items; or one CTA per item) on
+ * projection pass with each work-item size (1, 2, 4, 8, 16 or 32 groups of
+ * 2048 pixels) and grid (two persistent CTAs per SM, each on a contiguous run
+ * of items; or one CTA per item) on
  * `pages` and keeps the fastest for later calls on this workspace.
  * Synchronizes `stream`; call it outside stream capture.  chosen (host, 2
  * ints, or NULL) receives the groups per item and the CTAs per SM (0 = one

@@ -481,13 +481,15 @@ int cva_batch_tune(cva_batch* b, const cva_page* pages, int n, void* stream, int
         cudaEventDestroy(e0);
         return CVA_ERR_CUDA;
     }
-    static const int kGpi[] = {2, 4, 8, 16, 32};
+    // the candidates stated in cva.h: 1, 2, 4, 8, 16 or 32 groups a work item
+    static const int kGpi[] = {1, 2, 4, 8, 16, 32};
     static const int kGrid[] = {2, 0};
+    constexpr int NGPI = static_cast<int>(sizeof(kGpi) / sizeof(kGpi[0]));
     float best = 0.0f;
     int best_gpi = b->gpi, best_grid = b->grid_per_sm;
     bool fail = false;
     for (int gi = 0; gi < 2 && !fail; ++gi)
-        for (int pi = 0; pi < 5 && !fail; ++pi) {
+        for (int pi = 0; pi < NGPI && !fail; ++pi) {
             b->gpi = kGpi[pi];
             b->grid_per_sm = kGrid[gi];
             if (plan_batch(b, pages, n, &plan) != CVA_OK || upload_pages(b, n, s) != cudaSuccess) {

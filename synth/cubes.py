@@ -200,8 +200,9 @@ def _class_map(rng: np.random.Generator, H: int, W: int, K: int, both: bool) -> 
 # ----------------------------------------------------------------------------
 
 def _draw_pixels(rng: np.random.Generator, cmap: np.ndarray, means: np.ndarray,
-                 covs: np.ndarray, chunk: int = 1 << 20) -> np.ndarray:
-    """Gaussian pixels per class, rounded and clipped to 12 bits, planar.
+                 covs: np.ndarray, chunk: int = 1 << 20, max_dn: int = _MAX_DN) -> np.ndarray:
+    """Gaussian pixels per class, rounded and clipped to 0..max_dn (12 bits
+    by default), planar.
 
     Pixels are drawn in raster-order chunks: one standard normal vector per
     pixel, coloured by the Cholesky factor of its class covariance."""
@@ -223,7 +224,7 @@ def _draw_pixels(rng: np.random.Generator, cmap: np.ndarray, means: np.ndarray,
             if idx.size:
                 x[:, idx] = chols[c] @ z[:, idx] + mus[c]
         np.rint(x, out=x)
-        np.clip(x, 0, _MAX_DN, out=x)
+        np.clip(x, 0, max_dn, out=x)
         cube[:, s:e] = x
     return cube.reshape(B, H, W)
 
@@ -272,17 +273,22 @@ def _training_labels(rng: np.random.Generator, cmap: np.ndarray, n_train: Sequen
 
 def make_workload(seed: int, B: int, H: int, W: int, K: int, n_train: Sequence[int], k: int,
                   separation: Optional[Tuple[float, float]] = None, both: bool = True,
-                  cap_frac: float = 0.8, name: str = "custom") -> Workload:
-    """Draw one cube, its class map and its training label map."""
+                  cap_frac: float = 0.8, name: str = "custom", means: Optional[np.ndarray] = None,
+                  covs: Optional[np.ndarray] = None, max_dn: int = _MAX_DN) -> Workload:
+    """Draw one cube, its class map and its training label map.  ``means``
+    (K x B) and ``covs`` (K x B x B), when given, replace the drawn class
+    spectra and covariances (and ``separation`` is not applied); ``max_dn``
+    is the largest pixel value (4095: 12-bit data)."""
     if len(n_train) != K:
         raise ValueError("n_train must give one count per class")
     rng = np.random.Generator(np.random.PCG64(seed))
-    means = _mean_spectra(rng, B, K)
-    covs = _covariances(rng, B, K)
-    if separation is not None:
-        means = _set_separation(rng, means, covs, separation)
+    if means is None or covs is None:
+        means = _mean_spectra(rng, B, K)
+        covs = _covariances(rng, B, K)
+        if separation is not None:
+            means = _set_separation(rng, means, covs, separation)
     cmap = _class_map(rng, H, W, K, both)
-    cube = _draw_pixels(rng, cmap, means, covs)
+    cube = _draw_pixels(rng, cmap, means, covs, max_dn=max_dn)
     labels, got = _training_labels(rng, cmap, n_train, cap_frac)
     return Workload(name=name, cube=cube, labels=labels, classmap=cmap, K=K, k=k,
                     n_train=got, seed=seed, means=means, covs=covs)
@@ -309,20 +315,38 @@ def named_workload(name: str) -> Workload:
     return make_workload(seed, B, H, W, K, n_train, k, separation=sep, both=both, name=name)
 
 
-def batch_workloads(count: int = 64, seed0: int = 100300, sizes: Optional[List[int]] = None) -> List[Workload]:
+def _batch_page(i: int, seed0: int, sizes: Optional[List[int]]) -> Workload:
+    """Page i of a batch (its own generators, so pages can be drawn in any
+    order or in parallel)."""
+    side_choices = sizes if sizes is not None else list(range(512, 3073, 128))
+    rng = np.random.Generator(np.random.PCG64(seed0 + i))
+    H = int(rng.choice(side_choices))
+    W = int(rng.choice(side_choices))
+    B = int(rng.integers(12, 24))
+    K = int(rng.integers(2, 7))
+    n_train = tuple(int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e5))))) for _ in range(K))
+    return make_workload(seed0 + 1000 + i, B, H, W, K, n_train, K - 1,
+                         separation=(1.0, 4.0), both=True, cap_frac=0.5,
+                         name=f"batch{i:02d}_{B}b_{H}x{W}_K{K}")
+
+
+def _batch_page_args(a):
+    return _batch_page(*a)
+
+
+def batch_workloads(count: int = 64, seed0: int = 100300, sizes: Optional[List[int]] = None,
+                    workers: int = 0) -> List[Workload]:
     """Uneven batch of pages: sides in {512, 640, ..., 3072}, 12-23 bands,
     2-6 classes, 1k-100k training pixels a class (at most half the class),
-    k = K - 1 variates."""
-    out = []
-    side_choices = sizes if sizes is not None else list(range(512, 3073, 128))
-    for i in range(count):
-        rng = np.random.Generator(np.random.PCG64(seed0 + i))
-        H = int(rng.choice(side_choices))
-        W = int(rng.choice(side_choices))
-        B = int(rng.integers(12, 24))
-        K = int(rng.integers(2, 7))
-        n_train = tuple(int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e5))))) for _ in range(K))
-        out.append(make_workload(seed0 + 1000 + i, B, H, W, K, n_train, K - 1,
-                                 separation=(1.0, 4.0), both=True, cap_frac=0.5,
-                                 name=f"batch{i:02d}_{B}b_{H}x{W}_K{K}"))
-    return out
+    k = K - 1 variates.  With ``workers`` > 1 the pages are drawn by that many
+    fresh ("spawn") processes; every page has its own seed, so the pages are
+    the same either way."""
+    args = [(i, seed0, sizes) for i in range(count)]
+    if workers > 1 and count > 1:
+        import multiprocessing
+        from concurrent.futures import ProcessPoolExecutor
+
+        with ProcessPoolExecutor(max_workers=min(workers, count),
+                                 mp_context=multiprocessing.get_context("spawn")) as ex:
+            return list(ex.map(_batch_page_args, args))
+    return [_batch_page(*a) for a in args]
