@@ -50,7 +50,7 @@ namespace {
 constexpr int TPB = 384;  // 12 warps: one column of the elimination fits one pass from column 5 on
 constexpr int NWARP = TPB / 32;
 constexpr int JACOBI_SWEEPS = 40;
-constexpr int REFINE_STEPS = 6;
+constexpr int REFINE_STEPS = 8;
 constexpr int MAXTRI = MAXB * (MAXB + 1) / 2;
 
 // Work space of the symmetric eigensolver for matrices of order <= NM.
@@ -69,11 +69,20 @@ struct SymEig {
     int rp[NM / 2], rq[NM / 2], rok[NM / 2];
     unsigned char rr[NM][NM];
     float red[3][NWARP];
-    float last_correction;  // largest entry of the last refinement correction
+    float last_correction;  // size of the last refinement correction (see sym_eig)
+    int rotated;            // a cluster rotation was applied in this step
 };
 
-// A refinement whose last correction is still this large did not converge.
-constexpr float REFINE_FAIL = 1e-2f;
+// The refinement stops once its correction is below REFINE_DONE; one that is
+// still at or above it after REFINE_STEPS steps did not converge.  After a
+// correction of size e the remaining error is of order e^2 (the iteration
+// converges quadratically), so a converged result is good to ~1e-12.
+constexpr float REFINE_DONE = 1e-6f;
+// Eigenvalues closer than this relative distance (to the smaller of the two)
+// are refined as one cluster: the cluster's subspace is refined, the basis
+// inside it is not resolved (its vectors are not determined to this
+// precision), and no correction divides by their gap.
+constexpr float CLUSTER_REL = 1e-7f;
 
 struct FinSmem {
     df A[MAXB][2 * MAXB + MAXK + 1];  // [Sw | Mb | I] during elimination
@@ -341,8 +350,71 @@ __device__ void jacobi_serial(SymEig<NM>& e)
 // whose matrix products are spread over the whole block.  Leaves the eigenvectors in e.W
 // (columns) and the eigenvalues in e.lam, unsorted.  Every thread of the
 // block calls it.
+//
+// The size of a correction E (W <- W (I + E)) is measured by what it changes
+// in the result.  For principal components (`canonical` false) the columns of
+// W are the output: the size is max |E_ab|.  For canonical variates the output
+// of column b is G w_b / sqrt(lambda_b), which a correction moves by
+// sum_a E_ab sqrt(lambda_a / lambda_b) (G w_a / sqrt(lambda_a)): the size is
+// max |E_ab| sqrt(lambda_a / lambda_b) over columns b of non-zero eigenvalue,
+// and columns of the eigenvalue-0 direction of T = G^T G (G w = 0 there, so
+// no correction along it reaches a canonical vector) do not count.
+//
+// Clusters.  A pair whose eigenvalue estimates are closer than the
+// iteration's error bound delta (absolute: about 1e-7 |T| after the FP32
+// start) is refined as a cluster, and the refinement leaves the rotation
+// inside it alone.  Eigenvalues far below the largest can fall into one
+// cluster with each other or with the eigenvalue 0 of T even though they
+// are well apart in relative terms; left alone, their vectors stay mixed at
+// the FP32 start's level, which for canonical variates mixes the small
+// eigenvalue with 0.  So whenever a pair of one cluster is still coupled
+// (|s_ab| of W^T T W above rounding), thread 0 diagonalizes that 2 x 2 block
+// by one Jacobi rotation of the two columns of W (and of T W), and the step
+// starts over from the rotated W; once the couplings are at rounding level,
+// delta falls and the pairs are refined individually.
 template <int NM>
-__device__ void sym_eig(SymEig<NM>& e, int n)
+__device__ bool cluster_rotations(SymEig<NM>& e, int n, float delta, float lm)
+{
+    bool rot = false;
+    #pragma unroll 1
+    for (int sweep = 0; sweep < 2; ++sweep) {
+        #pragma unroll 1
+        for (int a = 0; a < n; ++a) {
+            #pragma unroll 1
+            for (int b = a + 1; b < n; ++b) {
+                const float la = e.lam[a].hi, lb = e.lam[b].hi;
+                const float near = CLUSTER_REL * fminf(fabsf(la), fabsf(lb));
+                if (fabsf(lb - la) > fmaxf(delta, near)) continue;
+                df p = df_from(0.0f), q = df_from(0.0f), r = df_from(0.0f);
+                #pragma unroll 1
+                for (int i = 0; i < n; ++i) {
+                    p = df_fma(p, e.W[i][a], e.TW[i][a]);
+                    q = df_fma(q, e.W[i][a], e.TW[i][b]);
+                    r = df_fma(r, e.W[i][b], e.TW[i][b]);
+                }
+                if (!(fabsf(q.hi) > fmaxf(1e-6f * fabsf(r.hi - p.hi), 1e-12f * lm))) continue;
+                // rotation J = [[c, s], [-s, c]] with J^T [[p, q], [q, r]] J diagonal
+                const float zeta = (r.hi - p.hi) / (2.0f * q.hi);
+                const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+                const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = t * c;
+                #pragma unroll 1
+                for (int i = 0; i < n; ++i) {
+                    const df wa = e.W[i][a], wb = e.W[i][b];
+                    e.W[i][a] = df_sub(df_mulf(wa, c), df_mulf(wb, sn));
+                    e.W[i][b] = df_add(df_mulf(wa, sn), df_mulf(wb, c));
+                    const df ta = e.TW[i][a], tb = e.TW[i][b];
+                    e.TW[i][a] = df_sub(df_mulf(ta, c), df_mulf(tb, sn));
+                    e.TW[i][b] = df_add(df_mulf(ta, sn), df_mulf(tb, c));
+                }
+                rot = true;
+            }
+        }
+    }
+    return rot;
+}
+
+template <int NM>
+__device__ void sym_eig(SymEig<NM>& e, int n, bool canonical)
 {
     const int tid = threadIdx.x;
     if (n > 8) {
@@ -396,19 +468,30 @@ __device__ void sym_eig(SymEig<NM>& e, int n)
             e.lam[tid] = df_mul(e.S[tid][tid], df_add(df_from(1.0f), df_mul(r, df_add(df_from(1.0f), r))));
         }
         __syncthreads();
+        if (tid == 0) {
+            e.rotated = cluster_rotations(e, n, delta, lm) ? 1 : 0;
+            if (e.rotated) e.last_correction = 1.0f;  // not converged if the steps end here
+        }
+        __syncthreads();
+        if (e.rotated) continue;  // the step starts over from the rotated W
         float emax = 0.0f;
+        const float lnull = 1e-12f * lm;  // eigenvalue-0 columns (the rank test of the caller)
         for (int q = tid; q < nn; q += TPB) {
             const int a = q / n, b = q % n;
             df ev;
             const df gap = df_sub(e.lam[b], e.lam[a]);
-            if (a == b || fabsf(gap.hi) <= delta) {
+            const float la = e.lam[a].hi, lb = e.lam[b].hi;
+            const float near = CLUSTER_REL * fminf(fabsf(la), fabsf(lb));
+            if (a == b || fabsf(gap.hi) <= fmaxf(delta, near)) {
                 ev = df_mulf(e.R[a][b], 0.5f);
             } else {
                 const df num = df_fma(e.S[a][b], e.lam[b], e.R[a][b]);
                 ev = df_from(num.hi / gap.hi);
             }
             e.E[a][b] = ev;
-            emax = fmaxf(emax, fabsf(ev.hi));
+            float w = 1.0f;
+            if (canonical) w = (lb > lnull) ? sqrtf(fmaxf(la, 0.0f) / lb) : 0.0f;
+            emax = fmaxf(emax, fabsf(ev.hi) * w);
         }
         __syncthreads();  // E complete; the red rows are free again
         emax = block_maxf(e, emax, 0);
@@ -423,7 +506,7 @@ __device__ void sym_eig(SymEig<NM>& e, int n)
         for (int q = tid; q < nn; q += TPB) e.W[q / n][q % n] = df_add(e.W[q / n][q % n], e.TW[q / n][q % n]);
         __syncthreads();
         if (tid == 0) e.last_correction = emax;
-        if (emax < 1e-6f) break;  // the next correction would be below the double-float rounding
+        if (emax < REFINE_DONE) break;  // the next correction would be of order 1e-12
     }
 }
 
@@ -691,9 +774,9 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
     __syncthreads();
 
     // ---- 4. FP32 cyclic Jacobi on T, then 5. refinement ----------------------
-    sym_eig<MAXK>(sm.eig, K);
+    sym_eig<MAXK>(sm.eig, K, true);
     __syncthreads();
-    if (!(sm.eig.last_correction < REFINE_FAIL)) {
+    if (!(sm.eig.last_correction < REFINE_DONE)) {
         if (tid == 0) set_status(dm, CVA_ERR_NO_CONVERGENCE);
         return;
     }
@@ -718,18 +801,34 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
     }
     __syncthreads();
     const int r = sm.r_eff;
-    const float unscale = __frcp_rn(scale);  // a power of two: exact
-    if (tid < B) sm.lam[tid] = (tid < r) ? df_mulf(sm.eig.lam[sm.order[tid]], unscale) : df_from(0.0f);
     const int nv = nvec > B ? B : nvec;
     const int rr = r < nv ? r : nv;
-    __syncthreads();
-    for (int e = tid; e < B * rr; e += TPB) {
-        const int b = e / rr, j = e - (e / rr) * rr;
+    // g_j = G w_j for the r non-zero eigenpairs; lambda_j = |g_j|^2 (the
+    // Rayleigh quotient of T at w_j, formed from G: T's own rounding, of
+    // order 1e-14 |T|, would limit the relative accuracy of eigenvalues far
+    // below the largest) and u_j = g_j / |g_j|
+    for (int e = tid; e < B * r; e += TPB) {
+        const int b = e / r, j = e - (e / r) * r;
         const int w = sm.order[j];
         df s = df_from(0.0f);
         #pragma unroll 1
         for (int c = 0; c < K; ++c) s = df_fma(s, sm.G[b][c], sm.eig.W[c][w]);
-        sm.U[b][j] = df_mul(s, df_rsqrt(sm.lam[j]));
+        sm.U[b][j] = s;
+    }
+    __syncthreads();
+    for (int j = warp; j < MAXB; j += NWARP) {
+        df s = df_from(0.0f);
+        if (j < r && lane < B) s = df_mul(sm.U[lane][j], sm.U[lane][j]);
+        if (j < r) s = warp_sum_df(s);
+        if (lane == 0) {
+            sm.lam[j] = j < r ? s : df_from(0.0f);
+            if (j < r) sm.q[j] = df_rsqrt(s);
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < B * rr; e += TPB) {
+        const int b = e / rr, j = e - (e / rr) * rr;
+        sm.U[b][j] = df_mul(sm.U[b][j], sm.q[j]);
     }
     __syncthreads();
     if (nv > r) complete_basis(sm, B, r, nv);
@@ -892,9 +991,9 @@ __global__ void __launch_bounds__(TPB) k_pca_finalize(DevModel* __restrict__ dm,
         sm.eig.Wf[a][b] = (a == b) ? 1.0f : 0.0f;
     }
     __syncthreads();
-    sym_eig<MAXB>(sm.eig, B);
+    sym_eig<MAXB>(sm.eig, B, false);
     __syncthreads();
-    if (!(sm.eig.last_correction < REFINE_FAIL)) {
+    if (!(sm.eig.last_correction < REFINE_DONE)) {
         if (tid == 0) set_status(dm, CVA_ERR_NO_CONVERGENCE);
         return;
     }

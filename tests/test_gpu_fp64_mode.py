@@ -4,9 +4,11 @@ form against the FP64 form, through the C ABI.
 Tolerances:
   * FP64 projections, stored as float32: max |y - y_ref| / max |y_ref| <= 2e-7
     per variate (one float rounding of an FP64 result);
-  * FP64-form 8-bit images: identical to the oracle's on >= 99.999 % of pixels,
-    within one level everywhere (a code differs only where an FP64 score sits
-    within rounding of a bin edge);
+  * FP64-form 8-bit images: identical to the oracle's at every pixel whose
+    oracle score is not within 1e-9 (of a bin) of a bin edge, and within one
+    level at those (a code can differ only where an FP64 score sits within
+    rounding of an edge; with one band and integer data whole groups of
+    pixels sit exactly on edges);
   * mixed (FP32) projections against the FP64 form: relative 1e-4, the bound
     the mixed form is held to.
 """
@@ -37,10 +39,17 @@ def _normwise(y, yref):
     return (np.abs(y - yref).max(axis=1) / np.abs(yref).max(axis=1)).max()
 
 
-def _codes_match(u, uref):
+def _codes_match(u, uref, y=None, rng=None):
     d = np.abs(u.astype(np.int32) - uref.astype(np.int32))
     assert d.max() <= 1
-    assert (d == 0).mean() >= 0.99999
+    if y is None:
+        assert (d == 0).mean() >= 0.99999
+        return
+    # the oracle's unrounded code position 255 (y - lo) / (hi - lo) + 1/2
+    lo, hi = rng[0::2][:, None], rng[1::2][:, None]
+    t = 255.0 * (y - lo) / (hi - lo) + 0.5
+    edge = np.abs(t - np.rint(t)) <= 1e-9
+    assert (d[~edge] == 0).all()
 
 
 CASES = [
@@ -78,14 +87,15 @@ def test_fp64_form_matches_oracle(case):
 
     out = torch.empty((k, H, W), dtype=torch.uint8, device=DEV)
     cva.cva_project_u8(cube, m, k, cva.CVA_RANGE_TRAINING, out)
-    _codes_match(out.cpu().numpy().reshape(k, w.P), oracle.to_u8(y_own, r_tr))
+    _codes_match(out.cpu().numpy().reshape(k, w.P), oracle.to_u8(y_own, r_tr), y_own, r_tr)
     cva.cva_project_u8(cube, m, k, cva.CVA_RANGE_GLOBAL, out)
-    _codes_match(out.cpu().numpy().reshape(k, w.P), oracle.to_u8(y_own, r_glob))
+    _codes_match(out.cpu().numpy().reshape(k, w.P), oracle.to_u8(y_own, r_glob), y_own, r_glob)
     given = np.empty(2 * k, np.float32)
     given[0::2] = np.percentile(y_own, 2, axis=1)
     given[1::2] = np.percentile(y_own, 97, axis=1)
     cva.cva_project_u8(cube, m, k, cva.CVA_RANGE_GIVEN, out, range=_to_dev(given))
-    _codes_match(out.cpu().numpy().reshape(k, w.P), oracle.to_u8(y_own, given.astype(np.float64)))
+    _codes_match(out.cpu().numpy().reshape(k, w.P), oracle.to_u8(y_own, given.astype(np.float64)), y_own,
+                 given.astype(np.float64))
     m.close()
 
 
