@@ -248,6 +248,12 @@ def cva_fit_project_u8_noalloc(cube: torch.Tensor, labels: torch.Tensor, K: int,
     B, H, W = cube.shape
     if tuple(labels.shape) != (H, W):
         raise ValueError("labels must be H x W")
+    if tuple(out.shape) != (k, H, W):
+        raise ValueError("out must be k x H x W")
+    if eigvals is not None and eigvals.numel() < B:
+        raise ValueError("eigvals must hold B doubles")
+    if status is not None and status.numel() < 1:
+        raise ValueError("status must hold one int")
     rc = load().cva_fit_project_u8_noalloc(_dptr(cube, torch.uint16, "cube"), B, H, W,
                                            _dptr(labels, torch.uint8, "labels"), K, k,
                                            _dptr(out, torch.uint8, "out"),

@@ -13,7 +13,9 @@
 //
 // In host code `g_noalloc_scratch` names a host-side stand-in, not device
 // memory: its device address is looked up with cudaGetSymbolAddress, once per
-// device, by the first call made with that device current.
+// device, by the first call made with that device current, and kept for the
+// life of the process (a cudaDeviceReset reloads the module elsewhere, so the
+// header rules out calls after one).
 #include <mutex>
 
 #include "cva_internal.cuh"
