@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--no-precision", action="store_true", help="skip the FP64-form comparison")
     ap.add_argument("--no-forms", action="store_true", help="batch workload: skip the per-page forms")
     ap.add_argument("--pages", type=int, default=64, help="batch workload: number of pages (64 = the benchmark)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations (small page, large cube, 64-page batch) in the line")
     return ap.parse_args()
 
 
@@ -163,109 +165,115 @@ class ClockSampler:
                 "power_w_max": max((num(r[3]) or 0) for r in loaded)}
 
 
-def _oracle_step_time(w, rows, keep=None):
-    """Oracle fit on the whole cube plus projection, training range and 8-bit
-    rescale of the first `rows` image rows; returns (t_fit, t_rows).  With a
-    dict `keep`, the oracle's fit, projection rows, range and codes go there."""
-    import numpy as np
+def _host_cores():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:  # noqa: BLE001 - platforms without affinity masks
+        return os.cpu_count() or 1
 
-    import oracle
 
-    t0 = time.perf_counter()
-    f = oracle.fit(w.cube, w.labels, w.K)
-    y_tr = None
-    lab = w.labels.reshape(-1)
-    tr_idx = np.flatnonzero(lab)
-    # the training range needs the training pixels' scores
-    sub = w.cube.reshape(w.B, -1)[:, tr_idx]
-    y_tr = oracle.project(sub.reshape(w.B, 1, -1), f["V"], f["mu"], w.k)
-    rng = oracle.range_global(y_tr)
-    t1 = time.perf_counter()
-    p1 = rows * w.W
-    y = oracle.project(w.cube, f["V"], f["mu"], w.k, 0, p1)
-    u8 = oracle.to_u8(y, rng)
-    t2 = time.perf_counter()
-    if keep is not None:
-        keep.update(fit=f, y=y, u8=u8, rows=rows)
-    return t1 - t0, t2 - t1
+class OracleTimer:
+    """The FP64 oracle on one page with a given number of threads.  The fit
+    (class statistics and scatter of the training pixels, eigensolve, and the
+    training pixels' scores for the training-score range) is timed as one
+    piece on the whole page; the per-pixel part (projection and 8-bit
+    rescale) is timed on bands of image rows and scaled to the page."""
+
+    def __init__(self, w, threads):
+        import oracle
+
+        self.oracle = oracle
+        self.w = w
+        self.threads = oracle.use_threads(threads)
+        self.f = None
+        self.rng = None
+
+    def fit(self):
+        import numpy as np
+
+        o, w = self.oracle, self.w
+        t0 = time.perf_counter()
+        f = o.fit(w.cube, w.labels, w.K)
+        tr = np.flatnonzero(w.labels.reshape(-1))
+        sub = w.cube.reshape(w.B, -1)[:, tr].reshape(w.B, 1, -1)
+        rng = o.range_global(o.project(sub, f["V"], f["mu"], w.k))
+        t = time.perf_counter() - t0
+        self.f, self.rng = f, rng
+        return t
+
+    def band(self, r0, rows, keep=None):
+        o, w = self.oracle, self.w
+        t0 = time.perf_counter()
+        y = o.project(w.cube, self.f["V"], self.f["mu"], w.k, r0 * w.W, (r0 + rows) * w.W)
+        u8 = o.to_u8(y, self.rng)
+        t = time.perf_counter() - t0
+        if keep is not None:
+            keep.update(fit=self.f, y=y, u8=u8, rows=rows, r0=r0)
+        return t
+
+    def rows_for(self, seconds_per_band):
+        """Band height whose projection takes about `seconds_per_band`."""
+        rows = min(self.w.H, 16)
+        t = self.band(0, rows)
+        return int(max(1, min(self.w.H, rows * seconds_per_band / max(t, 1e-6))))
+
+
+def _cpu_baseline(w, seconds, threads):
+    """Mpixel/s of the oracle on the page with `threads` threads, from about
+    `seconds` of CPU work: the median of three whole-page fits plus the median
+    band time scaled to all rows."""
+    T = OracleTimer(w, threads)
+    fits = [T.fit() for _ in range(3 if seconds > 2.0 else 1)]
+    tf = statistics.median(fits)
+    rows = T.rows_for(max(0.05, (seconds - sum(fits)) / 8))
+    bands = []
+    for i in range(8):
+        r0 = (i * 977) % max(1, w.H - rows + 1)
+        bands.append(T.band(r0, rows) * w.H / rows)
+    tp = statistics.median(bands)
+    t = tf + tp
+    return {"value": w.P / t / 1e6, "unit": UNIT, "cores": T.threads, "kind": "oracle",
+            "ms_per_page": t * 1e3, "fit_ms": tf * 1e3, "per_pixel_ms": tp * 1e3,
+            "sample": (f"the oracle's whole-page fit with the training-score range (median of {len(fits)}) plus its "
+                       f"projection and 8-bit rescale timed on 8 bands of {rows} of {w.H} rows and scaled to the "
+                       f"page, {T.threads} thread(s)")}
 
 
 REFERENCE_BUDGET_S = 90.0  # wall time of the whole --impl reference run, all steps
-
-
-def _oracle_band_time(w, r0, rows):
-    """Oracle on the row band [r0, r0 + rows) of the page as a page of its own:
-    fit on the band's training pixels, training range, projection and 8-bit
-    rescale of every band pixel.  Returns the seconds taken, or None when the
-    band misses a class."""
-    import numpy as np
-
-    import oracle
-
-    cube = np.ascontiguousarray(w.cube[:, r0:r0 + rows])
-    lab = np.ascontiguousarray(w.labels[r0:r0 + rows])
-    t0 = time.perf_counter()
-    try:
-        f = oracle.fit(cube, lab, w.K)
-    except oracle.OracleError:
-        return None
-    y = oracle.project(cube, f["V"], f["mu"], w.k)
-    oracle.to_u8(y, oracle.range_training(y, lab))
-    return time.perf_counter() - t0
-
-
-CPU_BASELINE_S = 12.0  # CPU work of the oracle baseline beside the GPU line
+CPU_BASELINE_S = 8.0  # CPU work of each oracle baseline beside the GPU line
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e nominal bandwidth, reported beside the measured peak
 
 
-def _oracle_bands(w, seconds, steps=None):
-    """Oracle runs on row bands of the page (each a page of its own), the band
-    sized from a first timing so that `steps` runs (or as many as fit) take
-    about `seconds`.  Returns (median time scaled to the page, band rows,
-    runs)."""
-    rows = min(w.H, 256)
-    t = None
-    while t is None:  # a band that holds every class
-        t = _oracle_band_time(w, 0, rows)
-        if t is None:
-            if rows >= w.H:
-                raise SystemExit("no band of the page holds every class")
-            rows = min(w.H, rows * 2)
-    n = steps if steps is not None else max(3, int(seconds / max(t * 4, 1e-6)))
-    # the band may shrink below the first one; a band that misses a class is widened below
-    rows = int(max(32, min(w.H, rows * (seconds / n) / max(t, 1e-6))))
-    times = []
-    for i in range(n):
-        band = rows
-        tb = None
-        while tb is None:
-            r0 = (i * 977) % max(1, w.H - band + 1)
-            tb = _oracle_band_time(w, r0, band)
-            if tb is None:
-                band = min(w.H, band * 2)
-        times.append(tb * w.H / band)
-    return statistics.median(times), rows, n
-
-
 def run_reference(a):
-    """The FP64 oracle on the host cores, each step a row band of the page sized
-    so that the whole run stays within REFERENCE_BUDGET_S; the band's time is
-    scaled to the full page."""
+    """The FP64 oracle on every host core.  Each step is one page: the
+    whole-page fit (timed once, median of three) plus the projection and
+    8-bit rescale of a band of rows scaled to the page, the band sized so that
+    the whole run stays within REFERENCE_BUDGET_S."""
     world, rank, _ = _dist_env()
     if rank != 0:
         return
     w = _workload(a.workload, 0)
-    if a.warmup:
-        _oracle_bands(w, min(REFERENCE_BUDGET_S, 5.0), steps=a.warmup)
-    t, rows, _ = _oracle_bands(w, REFERENCE_BUDGET_S, steps=max(1, a.steps))
+    T = OracleTimer(w, _host_cores())
+    tf = statistics.median([T.fit() for _ in range(3)])
+    n = max(1, a.steps) + a.warmup
+    rows = T.rows_for(max(1e-3, (REFERENCE_BUDGET_S - 3 * tf) / n))
+    times = []
+    for i in range(n):
+        r0 = (i * 977) % max(1, w.H - rows + 1)
+        tb = T.band(r0, rows) * w.H / rows
+        if i >= a.warmup:
+            times.append(tf + tb)
+    t = statistics.median(times)
     value = w.P / t / 1e6
-    sample = (f"each step: the oracle on a band of {rows} of {w.H} rows taken as a page (fit on its training "
-              f"pixels, training range, projection and 8-bit rescale of all its pixels), time scaled to the full page")
+    sample = (f"each step: the oracle's whole-page fit with the training-score range (timed once, median of 3) "
+              f"plus its projection and 8-bit rescale on a band of {rows} of {w.H} rows scaled to the page, "
+              f"{T.threads} thread(s)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(w),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": T.threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -462,7 +470,7 @@ def _other_outputs(cva, torch, w, m, cube, stream, peak):
 
 def _errors_vs_oracle(cva, torch, w, m, cube, out, keep, stream):
     """Eigenvalues, canonical vectors (S_w norm), projections and codes of the
-    mixed form against the FP64 oracle (projection rows: the oracle's sample)."""
+    mixed form against the FP64 oracle (projection rows: the oracle's band)."""
     import numpy as np
 
     f = keep["fit"]
@@ -471,19 +479,154 @@ def _errors_vs_oracle(cva, torch, w, m, cube, out, keep, stream):
     lam_rel = np.abs(lam[:r] - f["lam"][:r]) / f["lam"][:r]
     Sw = f["Sw"]
     vs = [float(np.sqrt((V[:, j] - f["V"][:, j]) @ Sw @ (V[:, j] - f["V"][:, j]))) for j in range(min(r, w.k))]
-    p1 = keep["rows"] * w.W
+    p0, p1 = keep["r0"] * w.W, (keep["r0"] + keep["rows"]) * w.W
     yy = torch.empty((w.k, w.H, w.W), dtype=torch.float32, device=cube.device)
     with torch.cuda.stream(stream):
         cva.cva_project(cube, m, w.k, out_f32=yy, stream=stream)
     torch.cuda.synchronize()
-    yg = yy.reshape(w.k, -1)[:, :p1].cpu().numpy().astype(np.float64)
+    yg = yy.reshape(w.k, -1)[:, p0:p1].cpu().numpy().astype(np.float64)
+    del yy
     yr = keep["y"]
     rel = np.abs(yg - yr).max(axis=1) / np.abs(yr).max(axis=1)
-    ug = out.reshape(w.k, -1)[:, :p1].cpu().numpy().astype(np.int32)
+    ug = out.reshape(w.k, -1)[:, p0:p1].cpu().numpy().astype(np.int32)
     du = np.abs(ug - keep["u8"].astype(np.int32))
     return {"eigvals_rel_err": [float(v) for v in lam_rel], "eigvecs_sw_err": vs,
             "projection_rel_err_max": float(rel.max()), "u8_within_1": float((du <= 1).mean()),
-            "u8_identical": float((du == 0).mean()), "pixels_compared": int(p1)}
+            "u8_identical": float((du == 0).mean()), "pixels_compared": int(p1 - p0)}
+
+
+def _oracle_errors(cva, torch, w, m, cube, out, stream, rows=256):
+    """The oracle's fit of the page and a band of its rows, then
+    _errors_vs_oracle (not timed)."""
+    T = OracleTimer(w, _host_cores())
+    T.fit()
+    keep = {}
+    rows = min(w.H, max(1, rows * 4096 // max(w.W, 1)))
+    T.band((w.H - rows) // 2, rows, keep)
+    return _errors_vs_oracle(cva, torch, w, m, cube, out, keep, stream)
+
+
+def _both_baselines(w, seconds):
+    """The oracle's Mpixel/s on every host core, with the single-core figure
+    beside it."""
+    allc = _cpu_baseline(w, seconds / 2, _host_cores())
+    allc["one_core"] = _cpu_baseline(w, seconds, 1)
+    return allc
+
+
+# ---------------------------------------------------------------------------
+# extra workloads of the line, drawn in the background
+# ---------------------------------------------------------------------------
+
+LARGE_WORKLOAD = "cube23b_8192x6144_K6"
+SMALL_WORKLOAD = "cube16b_512x512_K3"
+BATCH_WORKLOAD = "batch64_uneven"
+
+
+def _start_extra_workloads(pages):
+    """Spawn processes drawing the large cube and the batch's pages (fresh
+    interpreters, so starting them after CUDA is initialized is safe; every
+    page has its own seed, so they are the same as drawn in order)."""
+    import multiprocessing
+    from concurrent.futures import ProcessPoolExecutor
+
+    from synth import cubes
+
+    pool = ProcessPoolExecutor(max_workers=max(1, min(16, _host_cores() - 1)),
+                               mp_context=multiprocessing.get_context("spawn"))
+    futs = {"large": pool.submit(cubes.named_workload, LARGE_WORKLOAD),
+            "batch": [pool.submit(cubes._batch_page, i, 100300, None) for i in range(pages)]}
+    return pool, futs
+
+
+def _collect_extra_workloads(pool, futs):
+    out = {}
+    try:
+        out["large"] = futs["large"].result()
+    except Exception as exc:  # noqa: BLE001 - reported in the line
+        out["large"] = exc
+    try:
+        out["batch"] = [f.result() for f in futs["batch"]]
+    except Exception as exc:  # noqa: BLE001 - reported in the line
+        out["batch"] = exc
+    pool.shutdown()
+    return out
+
+
+def _page_config(cva, torch, w, dev, steps, peak):
+    """One page of another configuration: fit + fused projection to 8 bits
+    (training-score range) as two replayed graphs, timed like the headline
+    step; the projection launch timed by events around its graph."""
+    cube = torch.from_numpy(w.cube).to(dev)
+    labels = torch.from_numpy(w.labels).to(dev)
+    out = torch.empty((w.k, w.H, w.W), dtype=torch.uint8, device=dev)
+    m = cva.Model(w.B, w.K)
+    cva.cva_model_reserve(m, int(sum(w.n_train)) + 1024)
+    cva.cva_set_variates(m, w.k)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        cva.cva_fit(cube, labels, w.K, m, stream=stream)
+        cva.cva_project_u8(cube, m, w.k, cva.CVA_RANGE_TRAINING, out, stream=stream)
+    torch.cuda.synchronize()
+    st = cva.cva_status(m, stream=stream)
+    if st != cva.CVA_OK:
+        raise RuntimeError(f"fit failed: {cva.cva_strerror(st)}")
+    g_fit = torch.cuda.CUDAGraph()
+    g_proj = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_fit, stream=stream):
+        cva.cva_fit(cube, labels, w.K, m, stream=stream)
+    with torch.cuda.graph(g_proj, stream=stream):
+        cva.cva_project_u8(cube, m, w.k, cva.CVA_RANGE_TRAINING, out, stream=stream)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            g_fit.replay()
+            g_proj.replay()
+    pa = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    pb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for i in range(steps):
+            g_fit.replay()
+            pa[i].record(stream)
+            g_proj.replay()
+            pb[i].record(stream)
+        t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    proj_ms = statistics.mean(pa[i].elapsed_time(pb[i]) for i in range(steps))
+    alg = w.P * (2 * w.B + w.k)
+    achieved = alg / (proj_ms * 1e-3) / 1e9
+    res = {"value": w.P / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "fit_ms": ms - proj_ms,
+           "steps": steps, "dtype": "f32", "config": _config(w),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "kernel": "k_project_v8 (fused projection + u8)",
+                        "alg_bytes_per_launch": alg, "launch_ms": proj_ms}}
+    res["err_vs_oracle"] = _extra(_oracle_errors, cva, torch, w, m, cube, out, stream)
+    m.close()
+    return res
+
+
+def _ragged_page(cva, torch, w, dev, steps, peak):
+    """The benchmark page cropped to odd sides (H - 3) x (W - 1), so that its
+    pixel count is not a multiple of 8 and no band starts on 16 bytes: the
+    same fit + fused projection timed like the headline step."""
+    import dataclasses
+
+    import numpy as np
+
+    H, W = w.H - 3, w.W - 1
+    lab = np.ascontiguousarray(w.labels[:H, :W])
+    w2 = dataclasses.replace(w, name=f"{w.name}_cropped_{H}x{W}", cube=np.ascontiguousarray(w.cube[:, :H, :W]),
+                             labels=lab, classmap=np.ascontiguousarray(w.classmap[:H, :W]),
+                             n_train=tuple(int((lab == c + 1).sum()) for c in range(w.K)))
+    res = _page_config(cva, torch, w2, dev, steps, peak)
+    res["pixels_mod_8"] = w2.P % 8
+    res["roofline"]["kernel"] = "k_project_r8 (ragged fused projection + u8)"
+    return res
 
 
 def run_ours(a):
@@ -629,6 +772,14 @@ def run_ours(a):
     st = cva.cva_status(m, stream=stream)
     if st != cva.CVA_OK:
         raise SystemExit(f"fit failed during timing: {cva.cva_strerror(st)}")
+    del cube_e, lab_e, out_e
+
+    # the other configurations' pages are drawn by spawn processes from here
+    # on (not during the timed regions above: their host load would show in
+    # the graph launches and the host copies)
+    extras = None
+    if rank == 0 and world == 1 and not a.no_extras:
+        extras = _start_extra_workloads(a.pages)
 
     precision = None
     if rank == 0 and not a.no_precision:
@@ -639,6 +790,7 @@ def run_ours(a):
         others = _extra(_other_outputs, cva, torch, w, m, cube, stream, _peaks()[0])
         others["page_stream"] = _extra(_page_stream, cva, torch, w, cube, labels, out, stream,
                                        max(20, min(a.steps, 200)))
+        others["ragged_page"] = _extra(_ragged_page, cva, torch, w, dev, max(20, min(a.steps, 200)), _peaks()[0])
 
     if rank == 0:
         peak, peak_kind = _peaks()
@@ -669,29 +821,50 @@ def run_ours(a):
             "precision": precision,
             "other_outputs": others,
         }
+
+        # the other configurations, each on its own page(s)
+        configs = None
+        if extras is not None:
+            from synth import named_workload
+
+            drawn = _collect_extra_workloads(*extras)
+            cfg_steps = max(20, min(a.steps, 200))
+            configs = {}
+            configs[SMALL_WORKLOAD] = _extra(_page_config, cva, torch, named_workload(SMALL_WORKLOAD), dev,
+                                             cfg_steps, peak)
+            large = drawn["large"]
+            configs[LARGE_WORKLOAD] = (_extra(_page_config, cva, torch, large, dev, max(10, cfg_steps // 4), peak)
+                                       if not isinstance(large, Exception)
+                                       else {"error": f"{type(large).__name__}: {large}"})
+            batch = drawn["batch"]
+            configs[BATCH_WORKLOAD] = (_extra(_batch_measure, cva, torch, batch, dev, max(10, cfg_steps // 4),
+                                              forms=("mixed",))
+                                       if not isinstance(batch, Exception)
+                                       else {"error": f"{type(batch).__name__}: {batch}"})
+            line["configs"] = configs
+            torch.cuda.empty_cache()
+
+        # the oracle last, with no other work on the host cores
         if not a.no_cpu_baseline and world == 1:
-            rows = max(1, min(w.H, 256 * 4096 // max(w.W, 1)))
-            keep = {}
-            errs = _extra(lambda: (_oracle_step_time(w, rows, keep),
-                                   _errors_vs_oracle(cva, torch, w, m, cube, out, keep, stream))[1])
+            errs = _extra(_oracle_errors, cva, torch, w, m, cube, out, stream)
             if precision is not None:
                 precision["err_vs_oracle"] = errs
-            try:
-                t, band, nb = _oracle_bands(w, CPU_BASELINE_S)
-                line["cpu_baseline"] = {
-                    "value": P / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-                    "sample": (f"median of {nb} runs of the oracle on a band of {band} of {w.H} rows taken as a "
-                               f"page (fit, training range, projection, 8-bit rescale), about "
-                               f"{CPU_BASELINE_S:.0f} s in all, time scaled to the full page")}
-            except Exception as exc:  # noqa: BLE001 - reported in the line
-                line["cpu_baseline"] = {"error": f"{type(exc).__name__}: {exc}", "kind": "oracle"}
+            else:
+                line["err_vs_oracle"] = errs
+            line["cpu_baseline"] = _extra(_both_baselines, w, CPU_BASELINE_S)
+            if configs is not None:
+                if "error" not in configs[SMALL_WORKLOAD]:
+                    configs[SMALL_WORKLOAD]["cpu_baseline"] = _extra(_both_baselines, named_workload(SMALL_WORKLOAD),
+                                                                     2.0)
+                if "error" not in configs[LARGE_WORKLOAD]:
+                    configs[LARGE_WORKLOAD]["cpu_baseline"] = _extra(_both_baselines, drawn["large"],
+                                                                     CPU_BASELINE_S)
+                if "error" not in configs[BATCH_WORKLOAD]:
+                    configs[BATCH_WORKLOAD]["cpu_baseline"] = _extra(_batch_baselines, drawn["batch"])
         print(json.dumps(line), flush=True)
     m.close()
     if dist is not None:
         dist.destroy_process_group()
-
-
-BATCH_WORKLOAD = "batch64_uneven"
 
 
 def _batch_config(ws):
@@ -706,55 +879,40 @@ def _batch_config(ws):
             "l2": _l2_note(nb)}
 
 
-def _oracle_batch_time(ws, pages=2, rows=128):
-    """Oracle on a bounded sample of the batch: full fit of the first pages and
-    projection + rescale of `rows` rows of each, scaled to all pixels."""
-    t_fit = 0.0
-    t_px = 0.0
-    n_px = 0
-    fit_px = 0
-    for w in ws[:pages]:
-        tf, tr = _oracle_step_time(w, min(rows, w.H))
-        t_fit += tf
-        fit_px += w.P
-        t_px += tr
-        n_px += min(rows, w.H) * w.W
+def _batch_cpu_time(ws, threads, rows=8):
+    """Oracle seconds for the whole batch with `threads` threads: every
+    page's fit, plus its projection and 8-bit rescale on a band of `rows`
+    rows scaled to the page."""
+    t = 0.0
+    used = 1
+    for w in ws:
+        T = OracleTimer(w, threads)
+        used = T.threads
+        t += T.fit()
+        r = min(rows, w.H)
+        t += T.band((w.H - r) // 2, r) * w.H / r
+    return t, used
+
+
+def _batch_baselines(ws):
     P = sum(w.P for w in ws)
-    est = t_fit * (P / fit_px) + t_px * (P / n_px)
-    return est, (f"oracle fit of the first {pages} pages ({fit_px} px) + projection/8-bit rescale of {rows} rows "
-                 f"of each, scaled to the batch's {P} pixels")
+    res = {}
+    for key, threads in (("all", _host_cores()), ("one", 1)):
+        t, used = _batch_cpu_time(ws, threads)
+        res[key] = {"value": P / t / 1e6, "unit": UNIT, "cores": used, "kind": "oracle",
+                    "ms_per_batch": t * 1e3,
+                    "sample": "every page's whole fit with the training-score range, plus its projection and 8-bit "
+                              "rescale on a band of 8 rows scaled to the page, summed over the batch"}
+    out = res["all"]
+    out["one_core"] = res["one"]
+    return out
 
 
-def run_batch_bench(a):
-    import numpy as np
-    import torch
-
-    import paper_1612_06457_gb300 as cva
-    from synth import batch_workloads
-
-    world, rank, local = _dist_env()
-    if rank != 0:
-        return
-    ws = batch_workloads(a.pages)
-    if a.impl == "reference":
-        ts = []
-        for i in range(a.warmup + a.steps):
-            t, sample = _oracle_batch_time(ws)
-            if i >= a.warmup:
-                ts.append(t)
-        t = statistics.median(ts)
-        v = sum(w.P for w in ws) / t / 1e6
-        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
-                          "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                          "config": _batch_config(ws),
-                          "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-                          "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
-              flush=True)
-        return
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    cva.load()
+def _batch_measure(cva, torch, ws, dev, steps, forms=("mixed", "fp64"), warmup=3, sampler=None):
+    """The batched form on the pages `ws`: autotune, then the whole batch (one
+    graph) and its projection pass timed by CUDA events; the same pages
+    through the single-page entry points one after another (`forms`); end to
+    end from pinned host memory."""
     P = sum(w.P for w in ws)
     host = [(torch.from_numpy(w.cube).pin_memory(), torch.from_numpy(w.labels).pin_memory()) for w in ws]
     pages = [(c.to(dev), l.to(dev), w.K, w.k, torch.empty((w.k, w.H, w.W), dtype=torch.uint8, device=dev))
@@ -768,7 +926,7 @@ def run_batch_bench(a):
     torch.cuda.synchronize()
     st = cva.cva_batch_status(b, len(ws), stream=stream)
     if (st != cva.CVA_OK).any():
-        raise SystemExit(f"batch failed: {st.tolist()}")
+        raise RuntimeError(f"batch failed: {st.tolist()}")
     g_step = torch.cuda.CUDAGraph()
     g_proj = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g_step, stream=stream):
@@ -777,50 +935,50 @@ def run_batch_bench(a):
         cva.cva_project_batched(b, pages, stream=stream)
     torch.cuda.synchronize()
 
-    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
-    sampler.start()
+    if sampler is not None:
+        sampler.start()
     with torch.cuda.stream(stream):
-        for _ in range(a.warmup):
+        for _ in range(warmup):
             g_step.replay()
-    ms = _time_graphs(torch, (g_step,), stream, a.steps)
-    clocks = sampler.stop()
-    proj_ms = _time_graphs(torch, (g_proj,), stream, a.steps)
+    ms = _time_graphs(torch, (g_step,), stream, steps)
+    clocks = sampler.stop() if sampler is not None else None
+    proj_ms = _time_graphs(torch, (g_proj,), stream, steps)
 
     # the same pages one after another through the single-page entry points
     # (mixed form, then the FP64 form), each captured as one graph
-    forms = {}
-    form_list = () if a.no_forms else ((cva.CVA_PRECISION_MIXED, "per_page_mixed", max(3, a.steps // 4)),
-                                       (cva.CVA_PRECISION_FP64, "per_page_fp64", 3))
-    for mode, name, steps in form_list:
+    res_forms = {}
+    for name in forms:
+        mode = cva.CVA_PRECISION_MIXED if name == "mixed" else cva.CVA_PRECISION_FP64
+        fsteps = max(3, steps // 4) if name == "mixed" else 3
         models = []
         outs = []
         for w, p in zip(ws, pages):
-            m = cva.Model(w.B, w.K)
-            cva.cva_set_variates(m, w.k)
-            cva.cva_set_precision(m, mode)
-            models.append(m)
+            mm = cva.Model(w.B, w.K)
+            cva.cva_set_variates(mm, w.k)
+            cva.cva_set_precision(mm, mode)
+            models.append(mm)
             outs.append(torch.empty_like(p[4]))
         with torch.cuda.stream(stream):
-            for m, w, p, o in zip(models, ws, pages, outs):
-                cva.cva_fit(p[0], p[1], w.K, m, stream=stream)
-                cva.cva_project_u8(p[0], m, w.k, cva.CVA_RANGE_TRAINING, o, stream=stream)
+            for mm, w, p, o in zip(models, ws, pages, outs):
+                cva.cva_fit(p[0], p[1], w.K, mm, stream=stream)
+                cva.cva_project_u8(p[0], mm, w.k, cva.CVA_RANGE_TRAINING, o, stream=stream)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
-            for m, w, p, o in zip(models, ws, pages, outs):
-                cva.cva_fit(p[0], p[1], w.K, m, stream=stream)
-                cva.cva_project_u8(p[0], m, w.k, cva.CVA_RANGE_TRAINING, o, stream=stream)
-        t = _time_graphs(torch, (g,), stream, steps)
-        same = all(torch.equal(o, p[4]) for o, p in zip(outs, pages)) if mode == cva.CVA_PRECISION_MIXED else None
-        forms[name] = {"ms_per_step": t, "value": P / (t * 1e-3) / 1e6, "unit": UNIT, "steps": steps,
-                       "identical_images": same}
+            for mm, w, p, o in zip(models, ws, pages, outs):
+                cva.cva_fit(p[0], p[1], w.K, mm, stream=stream)
+                cva.cva_project_u8(p[0], mm, w.k, cva.CVA_RANGE_TRAINING, o, stream=stream)
+        t = _time_graphs(torch, (g,), stream, fsteps)
+        same = all(torch.equal(o, p[4]) for o, p in zip(outs, pages)) if name == "mixed" else None
+        res_forms["per_page_" + name] = {"ms_per_step": t, "value": P / (t * 1e-3) / 1e6, "unit": UNIT,
+                                         "steps": fsteps, "identical_images": same}
         del g
-        for m in models:
-            m.close()
+        for mm in models:
+            mm.close()
 
     # end to end: pinned host -> device, batch, images -> host
     outs_h = [torch.empty(p[4].shape, dtype=torch.uint8).pin_memory() for p in pages]
-    e2e_steps = max(2, min(a.steps, 5))
+    e2e_steps = max(2, min(steps, 5))
 
     def e2e_step():
         with torch.cuda.stream(stream):
@@ -845,10 +1003,9 @@ def run_batch_bench(a):
     peak, peak_kind = _peaks()
     alg = sum(w.P * (2 * w.B + w.k) for w in ws)
     achieved = alg / (proj_ms * 1e-3) / 1e9
-    line = {
-        "metric": METRIC, "value": P / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic", "config": _batch_config(ws),
+    res = {
+        "value": P / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+        "dtype": "f32", "config": _batch_config(ws),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "kb_project_v8 (batched fused projection + u8)",
                      "peak_kind": peak_kind, "alg_bytes_per_launch": alg, "launch_ms": proj_ms,
@@ -857,18 +1014,60 @@ def run_batch_bench(a):
                 "h2d_bytes_per_step": int(sum(w.cube.nbytes + w.labels.nbytes for w in ws)),
                 "d2h_bytes_per_step": int(sum(o.numel() for o in outs_h)), "ms_per_step": e2e_ms,
                 "steps": e2e_steps},
-        "gpu_launches": 11 * a.steps,
+        "gpu_launches": 11 * steps,
         "clocks": clocks,
         "autotuned": {"groups_per_item": tuned[0], "ctas_per_sm": tuned[1]},
-        "forms": forms,
+        "forms": res_forms,
     }
-    for name in forms:
-        line["speedup_over_" + name] = forms[name]["ms_per_step"] / ms
-    if not a.no_cpu_baseline:
-        t, sample = _oracle_batch_time(ws)
-        line["cpu_baseline"] = {"value": P / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
-    print(json.dumps(line), flush=True)
+    for name in res_forms:
+        res["speedup_over_" + name] = res_forms[name]["ms_per_step"] / ms
     b.close()
+    del pages, host
+    return res
+
+
+def run_batch_bench(a):
+    import torch
+
+    import paper_1612_06457_gb300 as cva
+    from synth import batch_workloads
+
+    world, rank, local = _dist_env()
+    if rank != 0:
+        return
+    ws = batch_workloads(a.pages, workers=_host_cores())
+    if a.impl == "reference":
+        ts = []
+        used = 1
+        for i in range(a.warmup + a.steps):
+            t, used = _batch_cpu_time(ws, _host_cores())
+            if i >= a.warmup:
+                ts.append(t)
+        t = statistics.median(ts)
+        v = sum(w.P for w in ws) / t / 1e6
+        sample = ("every page's whole fit with the training-score range, plus its projection and 8-bit rescale on "
+                  "a band of 8 rows scaled to the page, summed over the batch")
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+                          "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": _batch_config(ws),
+                          "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
+                                           "sample": sample},
+                          "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+              flush=True)
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cva.load()
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    res = _batch_measure(cva, torch, ws, dev, a.steps,
+                         forms=() if a.no_forms else ("mixed", "fp64"), warmup=a.warmup, sampler=sampler)
+    line = {"metric": METRIC, "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic"}
+    line.update(res)
+    if not a.no_cpu_baseline:
+        line["cpu_baseline"] = _batch_baselines(ws)
+    print(json.dumps(line), flush=True)
 
 
 def main():

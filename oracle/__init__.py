@@ -23,8 +23,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cva_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_lib = None        # the library the functions below call (plain or threaded)
+_libs = {}         # path -> loaded library
 
 OK = 0
 ERR_ARG = -1
@@ -40,26 +42,48 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, threaded: bool = False) -> str:
     """Compile ``cva_oracle.c`` into ``_build/liboracle.so`` (plain gcc -O2,
-    no fast-math, no FMA contraction, so x86 and Arm round alike)."""
+    no fast-math, no FMA contraction, so x86 and Arm round alike); with
+    ``threaded``, the same source with -fopenmp into ``liboracle_omp.so``
+    (identical results, used to time the oracle on every host core)."""
     os.makedirs(_BUILD, exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+    path = _OMP_PATH if threaded else _LIB_PATH
+    stale = (not os.path.exists(path)) or os.path.getmtime(path) < os.path.getmtime(_SRC)
     if force or stale:
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        tmp = path + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+               "-fno-fast-math"] + (["-fopenmp"] if threaded else []) + ["-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        os.replace(tmp, path)
+    return path
+
+
+def use_threads(n: int) -> int:
+    """Route the following oracle calls to the plain library (n <= 1) or to
+    the OpenMP build with n threads; returns the threads in effect."""
+    global _lib
+    lib = _open(build(threaded=n > 1))
+    with _lock:
+        _lib = lib
+    return int(lib.orc_threads(int(n) if n > 1 else 0))
 
 
 def _load():
     global _lib
+    if _lib is not None:
+        return _lib
+    lib = _open(build())
     with _lock:
-        if _lib is not None:
-            return _lib
-        path = build()
+        if _lib is None:
+            _lib = lib
+        return _lib
+
+
+def _open(path):
+    with _lock:
+        if path in _libs:
+            return _libs[path]
         lib = ctypes.CDLL(path)
         P = ctypes.c_void_p
         I64 = ctypes.c_int64
@@ -82,7 +106,9 @@ def _load():
             getattr(lib, name).restype = ctypes.c_int
         for name in ("orc_range_global", "orc_range_training", "orc_to_u8"):
             getattr(lib, name).restype = None
-        _lib = lib
+        lib.orc_threads.argtypes = [ctypes.c_int]
+        lib.orc_threads.restype = ctypes.c_int
+        _libs[path] = lib
         return lib
 
 

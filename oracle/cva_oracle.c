@@ -51,6 +51,14 @@
  *   - Sw is "not positive definite" when a Cholesky pivot falls to or below
  *     1e-12 times its own diagonal entry of Sw; no ridge is added.
  *
+ * Threads: built plainly this file is single-threaded.  Built with
+ * -fopenmp (a second library, used only to time the oracle on every host
+ * core) the per-pixel loops of the projection, the ranges, the rescales and
+ * the integer class sums run over the pixels in parallel; each of those
+ * results is independent of the order in which pixels are visited (one
+ * value per pixel, exact integer sums, min / max), so both builds give
+ * identical results.  The FP64 scatter sums stay serial for that reason.
+ *
  * Layouts: cube is band-sequential uint16 B x P (P = H W pixels, band b at
  * cube + b P); labels are uint8 P, 0 = not a training pixel, c + 1 = class c;
  * all matrices are row-major doubles; V column j is canonical vector j; a
@@ -60,6 +68,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_ERR_ARG (-1)
@@ -86,15 +97,17 @@ int orc_class_sums(const uint16_t* cube, int64_t B, int64_t P, const uint8_t* la
         n[c] = 0;
         for (int64_t b = 0; b < B; ++b) s[c * B + b] = 0;
     }
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : n[:K], s[:K * B]) reduction(| : bad)
     for (int64_t p = 0; p < P; ++p) {
         int64_t lab = labels[p];
         if (lab == 0) continue;
-        if (lab > K) return ORC_ERR_LABEL;
+        if (lab > K) { bad = 1; continue; }
         int64_t c = lab - 1;
         n[c] += 1;
         for (int64_t b = 0; b < B; ++b) s[c * B + b] += cube[b * P + p];
     }
-    return ORC_OK;
+    return bad ? ORC_ERR_LABEL : ORC_OK;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -324,6 +337,7 @@ int orc_project(const uint16_t* cube, int64_t B, int64_t P, int64_t p0, int64_t 
     if (B < 1 || k < 0 || k > ldv || p0 < 0 || p1 < p0 || p1 > P) return ORC_ERR_ARG;
     int64_t n = p1 - p0;
     for (int64_t j = 0; j < k; ++j) {
+#pragma omp parallel for schedule(static)
         for (int64_t p = p0; p < p1; ++p) {
             double acc = 0.0;
             for (int64_t b = 0; b < B; ++b) acc += V[b * ldv + j] * ((double)cube[b * P + p] - mu[b]);
@@ -342,6 +356,7 @@ void orc_range_global(const double* y, int64_t k, int64_t P, double* range)
 {
     for (int64_t j = 0; j < k; ++j) {
         double lo = INFINITY, hi = -INFINITY;
+#pragma omp parallel for schedule(static) reduction(min : lo) reduction(max : hi)
         for (int64_t p = 0; p < P; ++p) {
             double v = y[j * P + p];
             if (v < lo) lo = v;
@@ -358,6 +373,7 @@ void orc_range_training(const double* y, int64_t k, int64_t P, const uint8_t* la
 {
     for (int64_t j = 0; j < k; ++j) {
         double lo = INFINITY, hi = -INFINITY;
+#pragma omp parallel for schedule(static) reduction(min : lo) reduction(max : hi)
         for (int64_t p = 0; p < P; ++p) {
             if (labels[p] == 0) continue;
             double v = y[j * P + p];
@@ -374,6 +390,7 @@ void orc_to_u8(const double* y, int64_t k, int64_t P, const double* range, uint8
 {
     for (int64_t j = 0; j < k; ++j) {
         double lo = range[2 * j], hi = range[2 * j + 1];
+#pragma omp parallel for schedule(static)
         for (int64_t p = 0; p < P; ++p) {
             double v = 0.0;
             if (hi > lo) v = floor(255.0 * (y[j * P + p] - lo) / (hi - lo) + 0.5);
@@ -390,6 +407,7 @@ void orc_to_u16(const double* y, int64_t k, int64_t P, const double* range, uint
 {
     for (int64_t j = 0; j < k; ++j) {
         double lo = range[2 * j], hi = range[2 * j + 1];
+#pragma omp parallel for schedule(static)
         for (int64_t p = 0; p < P; ++p) {
             double v = 0.0;
             if (hi > lo) v = floor(65535.0 * (y[j * P + p] - lo) / (hi - lo) + 0.5);
@@ -521,4 +539,17 @@ int orc_cluster_indices(const double* y, int64_t k, int64_t P, const uint8_t* la
             DI[i * K + j] = smax > 0.0 ? (m - S[i] - S[j]) / smax : INFINITY;
         }
     return ORC_OK;
+}
+
+/* Threads the per-pixel loops use: sets them when n > 0 (OpenMP build only)
+ * and returns the number in effect (1 in the plain build). */
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

@@ -36,3 +36,25 @@ def test_a_failing_extra_measurement_is_reported_not_raised():
     r = bench._extra(boom, 3)
     assert r == {"error": "RuntimeError: extra failed on 3"}
     assert bench._extra(lambda a, b=2: a * b, 5, b=4) == 20
+
+
+def test_cpu_baselines_give_one_core_and_all_cores():
+    """The oracle baselines beside the GPU line: the whole-page fit plus a
+    band of the per-pixel work, on every host core and on one."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from synth import batch_workloads, make_workload
+
+    try:
+        w = make_workload(2024, 12, 160, 136, 3, (500, 400, 300), 2, separation=(1.0, 4.0), both=False)
+        d = bench._both_baselines(w, 0.5)
+        assert d["kind"] == "oracle" and d["value"] > 0 and d["unit"] == "Mpixel/s"
+        assert d["cores"] == bench._host_cores()
+        assert d["one_core"]["cores"] == 1 and d["one_core"]["value"] > 0
+        assert d["ms_per_page"] >= d["fit_ms"] > 0
+        ws = batch_workloads(3, sizes=[128, 256])
+        b = bench._batch_baselines(ws)
+        assert b["value"] > 0 and b["cores"] == bench._host_cores() and b["one_core"]["cores"] == 1
+    finally:
+        oracle.use_threads(1)
