@@ -17,9 +17,11 @@
 // pixel).  The main kernel (k_project_v8) gives each thread 8 consecutive
 // pixels, keeps 8 x k FP32 accumulators in registers, software-pipelines the
 // 16-byte band loads in batches of 8 so that up to 256 bytes per thread are
-// in flight, and writes 8-byte (u8) or 32-byte (f32) streaming stores.  A
-// scalar kernel covers pixel counts that are not a multiple of 8 and
-// unaligned buffers.
+// in flight, and writes 8-byte (u8) or 32-byte (f32) streaming stores.  Its
+// twin k_project_r8 takes cubes whose bands do not start on 16-byte
+// boundaries (P not a multiple of 8, or an unaligned cube) and unaligned
+// outputs at the same traffic: two aligned 16-byte loads per band and group,
+// funnel-shifted.  A scalar kernel is left for cubes of fewer than 32 pixels.
 //
 // The training-range kernel repeats the same FP32 operations, in the same
 // order, on the training pixels, so that the extreme training pixels land on
@@ -106,6 +108,12 @@ __device__ inline void reduce_range(ProjSmem<KV>& sm, float (&mn)[KV], float (&m
 // is computed, so up to 16 loads (256 bytes) per thread stay in flight while
 // the coefficients in shared memory are reused for 8 pixels.
 // ---------------------------------------------------------------------------
+// Bands per pipelined batch of the ragged kernel (two batches in flight): 8
+// up to 4 variates, 4 above, where 8 would spill the shuffled chunks (the
+// aligned kernel keeps 8: measured, its few spilled words cost less than
+// halving the bytes in flight).
+__host__ __device__ constexpr int ragged_batch_bands(int KV) { return KV <= 4 ? 8 : 4; }
+
 template <int KV>
 __device__ inline void accumulate8(float (&acc)[KV][8], const uint4& w, const float* vrow, float shift)
 {
@@ -137,37 +145,38 @@ __device__ __forceinline__ void project_group8(const uint16_t* __restrict__ cube
 {
     const long long plane = P / 8;  // band stride in uint4 units
     const uint4* src = reinterpret_cast<const uint4*>(cube) + g;
+    constexpr int NB = 8;
     float acc[KV][8];
     #pragma unroll
     for (int j = 0; j < KV; ++j)
         #pragma unroll
         for (int i = 0; i < 8; ++i) acc[j][i] = 0.0f;
-    uint4 wa[8], wb[8];
+    uint4 wa[NB], wb[NB];
     #pragma unroll
-    for (int u = 0; u < 8; ++u)
+    for (int u = 0; u < NB; ++u)
         if (u < B) wa[u] = __ldcs(src + u * plane);
-    for (int b0 = 0;; b0 += 16) {
+    for (int b0 = 0;; b0 += 2 * NB) {
         // the batch tests are the same for every thread: whole batches are
         // skipped by branches, only a partial last batch is predicated
-        const bool second = b0 + 8 < B;
+        const bool second = b0 + NB < B;
         if (second) {
             #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (b0 + 8 + u < B) wb[u] = __ldcs(src + (b0 + 8 + u) * plane);
+            for (int u = 0; u < NB; ++u)
+                if (b0 + NB + u < B) wb[u] = __ldcs(src + (b0 + NB + u) * plane);
         }
         #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < NB; ++u)
             if (b0 + u < B) accumulate8<KV>(acc, wa[u], sm.V[b0 + u], sm.shift[b0 + u]);
         if (!second) break;
-        const bool third = b0 + 16 < B;
+        const bool third = b0 + 2 * NB < B;
         if (third) {
             #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (b0 + 16 + u < B) wa[u] = __ldcs(src + (b0 + 16 + u) * plane);
+            for (int u = 0; u < NB; ++u)
+                if (b0 + 2 * NB + u < B) wa[u] = __ldcs(src + (b0 + 2 * NB + u) * plane);
         }
         #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (b0 + 8 + u < B) accumulate8<KV>(acc, wb[u], sm.V[b0 + 8 + u], sm.shift[b0 + 8 + u]);
+        for (int u = 0; u < NB; ++u)
+            if (b0 + NB + u < B) accumulate8<KV>(acc, wb[u], sm.V[b0 + NB + u], sm.shift[b0 + NB + u]);
         if (!third) break;
     }
     const long long p = g * 8;
@@ -217,6 +226,240 @@ k_project_v8(const uint16_t* __restrict__ cube, int B, long long P, const DevMod
     const long long stride = static_cast<long long>(gridDim.x) * TPB;
     for (long long g = static_cast<long long>(blockIdx.x) * TPB + threadIdx.x; g < ngroups; g += stride)
         project_group8<KV, F32, U8, RNG, false>(cube, B, P, g, sm, j0, KV, out_f32, out_u8, mn, mx);
+    if (RNG) reduce_range<KV>(sm, mn, mx, KV, range_acc, j0);
+}
+
+// ---------------------------------------------------------------------------
+// Ragged cubes (P % 8 != 0, or a cube that does not start on 16 bytes): band
+// b then starts sh[b] = (off + b P) mod 8 values into a 16-byte chunk of the
+// cube (A: the cube's address rounded down to 16 bytes, off: the cube's
+// offset from it in values), so the 8 values of a pixel group straddle two
+// aligned chunks: each lane loads one chunk per band, takes the next from the
+// neighbouring lane by a warp shuffle, and funnel-shifts the group's values
+// out of the pair (a warp projects 31 groups from 32 chunks), so a band costs
+// one 16-byte load per lane as in the aligned kernel.  Groups g in [g_lo, g_hi) keep every
+// chunk inside the cube: g_lo = 1 when off > 0 (the first chunk of band 0
+// starts before the cube), g_hi = floor((P - 15) / 8) (the second chunk of
+// the last band stays before its end); the few pixels outside them are
+// projected one per thread by the grid's last CTA.  Stores take the widest
+// width the alignment of each output plane allows.
+// ---------------------------------------------------------------------------
+struct RaggedBands {
+    long long c0[MAXB];  // chunk of A holding the first value of band b
+    int sh[MAXB];        // values of that chunk before band b starts
+};
+
+// Values s .. s + 7 of the 16 values in lo, hi (s uniform across the warp).
+__device__ __forceinline__ uint4 take8(const uint4& lo, const uint4& hi, int s)
+{
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    const uint32_t bits = static_cast<uint32_t>(s & 1) * 16u;
+    uint32_t r[4];
+    switch (s >> 1) {
+        case 0:
+            #pragma unroll
+            for (int i = 0; i < 4; ++i) r[i] = __funnelshift_r(w[i], w[i + 1], bits);
+            break;
+        case 1:
+            #pragma unroll
+            for (int i = 0; i < 4; ++i) r[i] = __funnelshift_r(w[i + 1], w[i + 2], bits);
+            break;
+        case 2:
+            #pragma unroll
+            for (int i = 0; i < 4; ++i) r[i] = __funnelshift_r(w[i + 2], w[i + 3], bits);
+            break;
+        default:
+            #pragma unroll
+            for (int i = 0; i < 4; ++i) r[i] = __funnelshift_r(w[i + 3], w[i + 4], bits);
+            break;
+    }
+    return make_uint4(r[0], r[1], r[2], r[3]);
+}
+
+// Store 8 consecutive bytes / floats at any alignment (the alignment is the
+// same for every thread of a plane, so the branches do not diverge).
+__device__ __forceinline__ void store8_u8(uint8_t* dst, uint32_t lo4, uint32_t hi4)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
+    if ((a & 7) == 0) {
+        __stcs(reinterpret_cast<uint2*>(dst), make_uint2(lo4, hi4));
+    } else if ((a & 3) == 0) {
+        __stcs(reinterpret_cast<unsigned int*>(dst), lo4);
+        __stcs(reinterpret_cast<unsigned int*>(dst) + 1, hi4);
+    } else if ((a & 1) == 0) {
+        unsigned short* d = reinterpret_cast<unsigned short*>(dst);
+        __stcs(d, static_cast<unsigned short>(lo4 & 0xFFFFu));
+        __stcs(d + 1, static_cast<unsigned short>(lo4 >> 16));
+        __stcs(d + 2, static_cast<unsigned short>(hi4 & 0xFFFFu));
+        __stcs(d + 3, static_cast<unsigned short>(hi4 >> 16));
+    } else {
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            dst[i] = static_cast<uint8_t>(lo4 >> (8 * i));
+            dst[4 + i] = static_cast<uint8_t>(hi4 >> (8 * i));
+        }
+    }
+}
+
+__device__ __forceinline__ void store8_f32(float* dst, const float (&y)[8])
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
+    if ((a & 15) == 0) {
+        __stcs(reinterpret_cast<float4*>(dst), make_float4(y[0], y[1], y[2], y[3]));
+        __stcs(reinterpret_cast<float4*>(dst) + 1, make_float4(y[4], y[5], y[6], y[7]));
+    } else if ((a & 7) == 0) {
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) __stcs(reinterpret_cast<float2*>(dst) + i, make_float2(y[2 * i], y[2 * i + 1]));
+    } else {
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) __stcs(dst + i, y[i]);
+    }
+}
+
+// 31 pixel groups gw .. gw + 30 of a ragged cube, one per lane of the warp:
+// lane l loads chunk c0[b] + gw + l of every band (one 16-byte load), and the
+// group of lane l < 31 takes its values from its own chunk and lane l + 1's
+// (a warp shuffle), so every band costs one load per lane, pipelined in
+// batches of 8 bands as in the aligned kernel.  Lanes past g_hi load the last
+// in-bounds chunk (needed by the lane before them) and store nothing.  Every
+// lane of the warp calls this with the same gw.
+template <int KV, bool F32, bool U8, bool RNG>
+__device__ __forceinline__ void project_warp_ragged(const uint4* __restrict__ A, const RaggedBands& rb, int B,
+                                                    long long P, long long gw, long long g_hi,
+                                                    const ProjSmem<KV>& sm, int j0, float* __restrict__ out_f32,
+                                                    uint8_t* __restrict__ out_u8, float (&mn)[KV], float (&mx)[KV])
+{
+    const int lane = threadIdx.x & 31;
+    const long long g = gw + lane;
+    const long long gc = g <= g_hi ? g : g_hi;  // chunk offset of this lane's load (in bounds)
+    const bool active = lane < 31 && g < g_hi;
+    float acc[KV][8];
+    #pragma unroll
+    for (int j = 0; j < KV; ++j)
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) acc[j][i] = 0.0f;
+    auto take = [&](const uint4& lo, int b) -> uint4 {
+        const int sh = rb.sh[b];
+        if (!sh) return lo;  // the band starts on 16 bytes: the chunk is the group
+        uint4 hi;
+        hi.x = __shfl_down_sync(0xFFFFFFFFu, lo.x, 1);
+        hi.y = __shfl_down_sync(0xFFFFFFFFu, lo.y, 1);
+        hi.z = __shfl_down_sync(0xFFFFFFFFu, lo.z, 1);
+        hi.w = __shfl_down_sync(0xFFFFFFFFu, lo.w, 1);
+        return take8(lo, hi, sh);
+    };
+    constexpr int NB = ragged_batch_bands(KV);
+    uint4 wa[NB], wb[NB];
+    #pragma unroll
+    for (int u = 0; u < NB; ++u)
+        if (u < B) wa[u] = __ldcs(A + rb.c0[u] + gc);
+    for (int b0 = 0;; b0 += 2 * NB) {
+        const bool second = b0 + NB < B;
+        if (second) {
+            #pragma unroll
+            for (int u = 0; u < NB; ++u)
+                if (b0 + NB + u < B) wb[u] = __ldcs(A + rb.c0[b0 + NB + u] + gc);
+        }
+        #pragma unroll
+        for (int u = 0; u < NB; ++u)
+            if (b0 + u < B) accumulate8<KV>(acc, take(wa[u], b0 + u), sm.V[b0 + u], sm.shift[b0 + u]);
+        if (!second) break;
+        const bool third = b0 + 2 * NB < B;
+        if (third) {
+            #pragma unroll
+            for (int u = 0; u < NB; ++u)
+                if (b0 + 2 * NB + u < B) wa[u] = __ldcs(A + rb.c0[b0 + 2 * NB + u] + gc);
+        }
+        #pragma unroll
+        for (int u = 0; u < NB; ++u)
+            if (b0 + NB + u < B) accumulate8<KV>(acc, take(wb[u], b0 + NB + u), sm.V[b0 + NB + u], sm.shift[b0 + NB + u]);
+        if (!third) break;
+    }
+    if (!active) return;
+    const long long p = g * 8;
+    #pragma unroll
+    for (int j = 0; j < KV; ++j) {
+        float y[8];
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) y[i] = __fsub_rn(acc[j][i], sm.d[j]);
+        if (F32) store8_f32(out_f32 + static_cast<long long>(j0 + j) * P + p, y);
+        if (U8) {
+            const float sc = sm.scale[j], of = sm.off[j];
+            uint32_t c[8];
+            #pragma unroll
+            for (int i = 0; i < 8; ++i) c[i] = to_code(y[i], sc, of);
+            store8_u8(out_u8 + static_cast<long long>(j0 + j) * P + p, c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24),
+                      c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24));
+        }
+        if (RNG) {
+            #pragma unroll
+            for (int i = 0; i < 8; ++i) { mn[j] = fminf(mn[j], y[i]); mx[j] = fmaxf(mx[j], y[i]); }
+        }
+    }
+}
+
+// One pixel, any alignment (the scalar kernel's arithmetic, in the same order).
+template <int KV, bool F32, bool U8, bool RNG>
+__device__ __forceinline__ void project_pixel(const uint16_t* __restrict__ cube, int B, long long P, long long p,
+                                              const ProjSmem<KV>& sm, int j0, int kc, float* __restrict__ out_f32,
+                                              uint8_t* __restrict__ out_u8, float (&mn)[KV], float (&mx)[KV])
+{
+    float acc[KV];
+    #pragma unroll
+    for (int j = 0; j < KV; ++j) acc[j] = 0.0f;
+    for (int b = 0; b < B; ++b) {
+        const uint32_t x = __ldcs(cube + static_cast<long long>(b) * P + p);
+        const float xs = __fsub_rn(u16_biased(x), sm.shift[b]);
+        #pragma unroll
+        for (int j = 0; j < KV; ++j) acc[j] = __fmaf_rn(sm.V[b][j], xs, acc[j]);
+    }
+    #pragma unroll
+    for (int j = 0; j < KV; ++j) {
+        if (j >= kc) break;
+        const float y = __fsub_rn(acc[j], sm.d[j]);
+        if (F32) out_f32[static_cast<long long>(j0 + j) * P + p] = y;
+        if (U8) out_u8[static_cast<long long>(j0 + j) * P + p] = static_cast<uint8_t>(to_code(y, sm.scale[j], sm.off[j]));
+        if (RNG) { mn[j] = fminf(mn[j], y); mx[j] = fmaxf(mx[j], y); }
+    }
+}
+
+template <int KV, bool F32, bool U8, bool RNG>
+__global__ void __launch_bounds__(TPB, 2)
+k_project_r8(const uint16_t* __restrict__ cube, int B, long long P, long long g_lo, long long g_hi,
+             const DevModel* __restrict__ dm, int j0, const float* __restrict__ u8_range,
+             float* __restrict__ out_f32, uint8_t* __restrict__ out_u8, float* __restrict__ range_acc)
+{
+    __shared__ ProjSmem<KV> sm;
+    __shared__ RaggedBands rb;
+    if (dm->status != 0 || !dm->fitted) return;
+    load_coefs<KV>(sm, dm, B, j0, KV, u8_range, U8);
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(cube);
+    const uint4* A = reinterpret_cast<const uint4*>(addr & ~static_cast<uintptr_t>(15));
+    const long long off = static_cast<long long>((addr & 15) >> 1);
+    if (threadIdx.x < MAXB) {
+        const long long e = off + static_cast<long long>(threadIdx.x) * P;
+        rb.c0[threadIdx.x] = e >> 3;
+        rb.sh[threadIdx.x] = static_cast<int>(e & 7);
+    }
+    __syncthreads();
+
+    float mn[KV], mx[KV];
+    #pragma unroll
+    for (int j = 0; j < KV; ++j) { mn[j] = __int_as_float(0x7F800000); mx[j] = __int_as_float(0xFF800000); }
+    // warp w takes groups g_lo + 31 w .. + 30, then strides over the grid's warps
+    const long long wid = (static_cast<long long>(blockIdx.x) * TPB + threadIdx.x) >> 5;
+    const long long nwarps = (static_cast<long long>(gridDim.x) * TPB) >> 5;
+    for (long long gw = g_lo + 31 * wid; gw < g_hi; gw += 31 * nwarps)
+        project_warp_ragged<KV, F32, U8, RNG>(A, rb, B, P, gw, g_hi, sm, j0, out_f32, out_u8, mn, mx);
+    // the pixels outside the groups: [0, 8 g_lo) and [8 g_hi, P), fewer than 32
+    if (blockIdx.x == gridDim.x - 1) {
+        const long long head = 8 * g_lo, tail0 = 8 * g_hi;
+        const long long n = head + (P - tail0);
+        for (long long t = threadIdx.x; t < n; t += TPB) {
+            const long long p = t < head ? t : tail0 + (t - head);
+            project_pixel<KV, F32, U8, RNG>(cube, B, P, p, sm, j0, KV, out_f32, out_u8, mn, mx);
+        }
+    }
     if (RNG) reduce_range<KV>(sm, mn, mx, KV, range_acc, j0);
 }
 
@@ -496,12 +739,51 @@ cudaError_t run_v8(const uint16_t* cube, int B, long long P, const DevModel* dm,
     return cudaGetLastError();
 }
 
+template <int KV, bool F32, bool U8, bool RNG>
+cudaError_t run_r8(const uint16_t* cube, int B, long long P, const DevModel* dm, int j0,
+                   const float* u8_range, float* out_f32, uint8_t* out_u8, float* range_acc,
+                   int num_sms, cudaStream_t s)
+{
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project_r8<KV, F32, U8, RNG>, TPB, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long off = static_cast<long long>((reinterpret_cast<uintptr_t>(cube) & 15) >> 1);
+    const long long g_lo = off > 0 ? 1 : 0;
+    const long long g_hi = (P - 15) / 8;  // caller guarantees P >= 32
+    const long long per_cta = 31LL * (TPB / 32);  // groups a CTA takes per round
+    long long grid = (g_hi - g_lo + per_cta - 1) / per_cta;
+    const long long cap = static_cast<long long>(num_sms) * per_sm;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    k_project_r8<KV, F32, U8, RNG><<<static_cast<unsigned>(grid), TPB, 0, s>>>(cube, B, P, g_lo, g_hi, dm, j0, u8_range,
+                                                                           out_f32, out_u8, range_acc);
+    return cudaGetLastError();
+}
+
+// The pixel-count limit below which the scalar kernel takes the whole cube.
+constexpr long long RAGGED_MIN_P = 32;
+
 template <bool F32, bool U8, bool RNG>
 cudaError_t run_chunk(const uint16_t* cube, int B, long long P, const DevModel* dm, int j0, int kc,
                       const float* u8_range, float* out_f32, uint8_t* out_u8, float* range_acc,
                       bool vec, int num_sms, cudaStream_t s)
 {
     long long p_tail = 0;
+    if (!vec && P >= RAGGED_MIN_P) {
+        switch (kc) {
+            case 1: return run_r8<1, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s);
+            case 2: return run_r8<2, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s);
+            case 3: return run_r8<3, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s);
+            case 4: return run_r8<4, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s);
+            case 5: return run_r8<5, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s);
+            case 6: return run_r8<6, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s);
+            case 7: return run_r8<7, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s);
+            default: return run_r8<8, F32, U8, RNG>(cube, B, P, dm, j0, u8_range, out_f32, out_u8, range_acc, num_sms, s);
+        }
+    }
     if (vec) {
         cudaError_t e = cudaSuccess;
         switch (kc) {
