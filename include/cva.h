@@ -140,6 +140,51 @@ int cva_set_variates(cva_model* m, int nvec);
 int cva_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, int K,
             cva_model* m, void* stream);
 
+/* ---- One page split over several GPUs ------------------------------------
+ * Section 2's scatter matrices are sums over the training pixels, so a page
+ * can be cut into parts (e.g. bands of rows, one per GPU) whose exact integer
+ * class moments add up to the page's.  Each part's process calls
+ * cva_fit_moments on its part, exports the moments with cva_model_moments,
+ * sums them over all parts (an int64 all-reduce: exact, so the merged fit is
+ * bit-identical to cva_fit on the whole page), and calls
+ * cva_fit_from_moments with the sum; that fit also forms the training-score
+ * range of its own part's training pixels, which cva_model_training_range
+ * exports; the parts' ranges merge by min / max (of the lo and of the hi
+ * entries) and cva_set_training_range installs the merged range, after which
+ * cva_project_u8 with CVA_RANGE_TRAINING on each part gives the page's
+ * 8-bit image part by part.  Every call is asynchronous on `stream`.
+ *
+ * Words of the moment array: K classes of (B+1)(B+2)/2 int64 each. */
+#define CVA_MOMENT_WORDS(B, K) ((K) * ((B) + 1) * ((B) + 2) / 2)
+
+/* The class moments of the labelled pixels of a cube (or of one part of a
+ * page): for each class c the sums over its training pixels of x'_a x'_b,
+ * a <= b, with x' = (x_0 .. x_{B-1}, 1), so that the count n_c and the band
+ * sums s_c are among them.  Kept in the model (and the part's training pixels
+ * in its training matrix); no eigensolve.  Arguments and device errors as for
+ * cva_fit. */
+int cva_fit_moments(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, int K, cva_model* m,
+                    void* stream);
+
+/* Copy the model's class moments to `moments` (device, CVA_MOMENT_WORDS(B, K)
+ * int64, 8-byte aligned): class c's entry (a, b), a <= b <= B, at
+ * c (B+1)(B+2)/2 + a (B+1) - a (a-1)/2 + (b - a). */
+int cva_model_moments(cva_model* m, int64_t* moments, void* stream);
+
+/* Replace the model's class moments by `moments` (device, layout of
+ * cva_model_moments; e.g. the sum over all parts of a page) and finish the
+ * fit from them: means, Sw, Sb, the eigensolve and the canonical vectors as
+ * in cva_fit, then the training-score range of the training pixels of the
+ * model's last cva_fit_moments (its own part).  CVA_PRECISION_MIXED only.
+ * Device errors go to the status word as for cva_fit. */
+int cva_fit_from_moments(cva_model* m, const int64_t* moments, void* stream);
+
+/* Copy out (device, 2 nvec float32, (lo, hi) pairs) the model's
+ * training-score range, or install a range in its place (e.g. the min / max
+ * merge of every part's range). */
+int cva_model_training_range(cva_model* m, float* range, void* stream);
+int cva_set_training_range(cva_model* m, const float* range, void* stream);
+
 /* Principal components instead of canonical variates (Section 2: the
  * unsupervised PCA of the whole page -- subtract the mean, form the
  * covariance matrix, take its eigenvectors, orthonormal -- and, with a mask,

@@ -129,6 +129,10 @@ cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const u
                                int K, DevModel* dm, uint16_t* xtr, unsigned int* tiles, unsigned int* list,
                                long long cap, int num_sms, cudaStream_t s);
 cudaError_t launch_fit_finalize(DevModel* dm, int B, int K, int nvec, cudaStream_t s);
+// The class moments as K x (B+1)(B+2)/2 int64 words (class-major, upper
+// triangle of the augmented moment matrix, row-major), and back.
+cudaError_t launch_moments_export(const DevModel* dm, int B, int K, long long* out, cudaStream_t s);
+cudaError_t launch_moments_import(DevModel* dm, int B, int K, const long long* in, cudaStream_t s);
 cudaError_t launch_train_range(int B, int K, const uint16_t* xtr, DevModel* dm, int nvec, int num_sms,
                                cudaStream_t s);
 cudaError_t launch_scatter_sb(DevModel* dm, int B, int K, cudaStream_t s);

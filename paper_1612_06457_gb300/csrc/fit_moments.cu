@@ -11,7 +11,9 @@
 //
 // Four kernels for one page; the label map is cut into tiles of 16384
 // labels, one CTA per tile in the label passes (each thread holds 64 labels
-// from four 128-bit loads in flight, compared four bytes at a time):
+// from four 128-bit loads in flight, compared four bytes at a time; tiles of
+// 32768 labels, one wave of CTAs, measured 19.4 + 29.5 us against 17.9 +
+// 22.9 us for the two passes):
 //   k_tile_count    training pixels of each class in the tile, and whether
 //                   the tile holds a label above K; the last CTA to finish
 //                   (atomic ticket, no waiting) then takes the prefix sums of
@@ -44,23 +46,24 @@ namespace {
 constexpr int TPB = 256;
 constexpr int TILE = LABEL_TILE;   // 16384 = TPB * 64
 constexpr int SUB = TPB * 16;      // 4096 labels: one 128-bit load per thread
+constexpr int NG = TILE / SUB;     // 16-label groups (128-bit loads) per thread: 4
 constexpr int UNIT = 256;          // rows per work unit of the moments pass
 constexpr int NW = TPB / 32;
 
-// The tile's 64 labels of this thread: four 16-byte groups, SUB apart.
+// The tile's 64 labels of this thread: NG 16-byte groups, SUB apart.
 __device__ inline void load_tile(const uint8_t* __restrict__ labels, long long t0, long long P, int vec,
-                                 uint32_t (&w)[4][4])
+                                 uint32_t (&w)[NG][4])
 {
     const int tid = threadIdx.x;
     if (vec && t0 + TILE <= P) {
         #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < NG; ++u) {
             const uint4 v = __ldcs(reinterpret_cast<const uint4*>(labels + t0 + u * SUB + 16LL * tid));
             w[u][0] = v.x; w[u][1] = v.y; w[u][2] = v.z; w[u][3] = v.w;
         }
     } else {
         #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < NG; ++u) {
             w[u][0] = w[u][1] = w[u][2] = w[u][3] = 0u;
             const long long p0 = t0 + u * SUB + 16LL * tid;
             for (int i = 0; i < 16; ++i)
@@ -223,13 +226,13 @@ __device__ __forceinline__ void tile_count_body(const uint8_t* __restrict__ labe
     __shared__ int last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) bad = 0;
-    uint32_t w[4][4];
+    uint32_t w[NG][4];
     load_tile(labels, static_cast<long long>(tile) * TILE, P, vec, w);
     unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
     const uint32_t kpat = static_cast<uint32_t>(K) * 0x01010101u;
     uint32_t over = 0;
     #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NG; ++u) {
         if ((w[u][0] | w[u][1] | w[u][2] | w[u][3]) == 0u) continue;
         count16(w[u], K, cnt);
         #pragma unroll
@@ -299,7 +302,7 @@ __device__ __forceinline__ void tile_compact_body(const uint8_t* __restrict__ la
     __shared__ unsigned int base[MAXK];
     const int tid = threadIdx.x;
     const long long t0 = static_cast<long long>(tile) * TILE;
-    uint32_t w[4][4];
+    uint32_t w[NG][4];
     load_tile(labels, t0, P, vec, w);
     if (tid < K) {
         unsigned int start = 0;
@@ -308,14 +311,14 @@ __device__ __forceinline__ void tile_compact_body(const uint8_t* __restrict__ la
     }
     unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
     #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < NG; ++u)
         if ((w[u][0] | w[u][1] | w[u][2] | w[u][3]) != 0u) count16(w[u], K, cnt);
     unsigned long long excl[4], total[4];
     block_scan_packed(cnt, (K + 3) >> 2, wsum, excl, total);  // also orders base[] before its reads
     // class by class: the 16-bit mask of the group's labels equal to c + 1,
     // then one store per set bit to consecutive rows
     #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NG; ++u) {
         if ((w[u][0] | w[u][1] | w[u][2] | w[u][3]) == 0u) continue;
         const unsigned int p0 = static_cast<unsigned int>(t0 + u * SUB + 16LL * tid);
         #pragma unroll 1
@@ -341,6 +344,19 @@ k_tile_compact(const uint8_t* __restrict__ labels, long long P, int K, int vec,
     tile_compact_body(labels, P, K, vec, tiles, dm->cls_count, list, blockIdx.x);
 }
 
+// A read-only 16-bit load that asks L2 to fetch 64 bytes around it: the
+// training pixels sit in short runs (4-23 pixels on average per class on the
+// benchmark page), so the default fetches mostly bring unused bytes; measured
+// on the 23-band 4096 x 4096 page the gather's DRAM reads drop from 74 MB to
+// 43 MB (the distinct 64-byte blocks its values occupy: 42.4 MB; 32-byte
+// sectors: 26.1 MB) at the same kernel time, which is bound by load latency.
+__device__ inline uint32_t ld_u16_l2_64(const uint16_t* p)
+{
+    unsigned short v;
+    asm volatile("ld.global.nc.L2::64B.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+
 // The augmented row (x_0 .. x_{B-1}, 1, 0 ..) of listed training pixel i,
 // all its band loads in flight, stored as one 16-byte-aligned row.
 __device__ __forceinline__ void gather_row(const uint16_t* __restrict__ cube, int B, long long P,
@@ -351,7 +367,7 @@ __device__ __forceinline__ void gather_row(const uint16_t* __restrict__ cube, in
     const uint16_t* src = cube + list[i];
     uint32_t xv[MAXB];
     #pragma unroll
-    for (int b = 0; b < MAXB; ++b) xv[b] = (b < B) ? static_cast<uint32_t>(__ldg(src + static_cast<long long>(b) * P)) : 0u;
+    for (int b = 0; b < MAXB; ++b) xv[b] = (b < B) ? ld_u16_l2_64(src + static_cast<long long>(b) * P) : 0u;
     uint4* grow = reinterpret_cast<uint4*>(xtr + static_cast<long long>(i) * BR);
     #pragma unroll
     for (int q = 0; q < (MAXB + 8) / 8; ++q) {
@@ -825,6 +841,43 @@ k_pca_moments(const uint16_t* __restrict__ cube, int B, long long P, const uint8
     moments_flush(dm, 0, nb, npair, pa, pb, acc);
 }
 
+// The exact moments of every class as a flat array: class c, then the upper
+// triangle a <= b of the (B+1) x (B+1) augmented moment matrix in row-major
+// order (entry (a, b) at c W + a (B+1) - a (a-1)/2 + (b - a), W = (B+1)(B+2)/2).
+__device__ inline int tri_index(int a, int b, int BA)
+{
+    return a * BA - a * (a - 1) / 2 + (b - a);
+}
+
+__global__ void k_moments_export(const DevModel* __restrict__ dm, int B, int K, long long* __restrict__ out)
+{
+    const int BA = B + 1, per = BA * (BA + 1) / 2;
+    const int nb = mom_shape(B).nb;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * per; i += gridDim.x * blockDim.x) {
+        const int c = i / per;
+        int q = i - c * per, a = 0;
+        while (q >= BA - a) { q -= BA - a; ++a; }
+        const int b = a + q;
+        out[i] = static_cast<long long>(dm->mom[c][blk_index(a >> 2, b >> 2, nb)][(a & 3) * 4 + (b & 3)]);
+    }
+}
+
+// The inverse: the given moments replace the model's (the entries outside
+// the augmented matrix are not read by the finalize).
+__global__ void k_moments_import(DevModel* __restrict__ dm, int B, int K, const long long* __restrict__ in)
+{
+    const int BA = B + 1, per = BA * (BA + 1) / 2;
+    const int nb = mom_shape(B).nb;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * per; i += gridDim.x * blockDim.x) {
+        const int c = i / per;
+        int q = i - c * per, a = 0;
+        while (q >= BA - a) { q -= BA - a; ++a; }
+        const int b = a + q;
+        dm->mom[c][blk_index(a >> 2, b >> 2, nb)][(a & 3) * 4 + (b & 3)] = static_cast<unsigned long long>(in[i]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) dm->fitted = 0;
+}
+
 // Clears class 0's moments and the fit state before a principal-component fit.
 __global__ void k_pca_reset(DevModel* __restrict__ dm, int B)
 {
@@ -908,6 +961,18 @@ cudaError_t launch_batch_moments(const PageDev* pages, int n, const BatchTotals*
 }  // namespace cva
 
 namespace cva {
+
+cudaError_t launch_moments_export(const DevModel* dm, int B, int K, long long* out, cudaStream_t s)
+{
+    k_moments_export<<<4, 256, 0, s>>>(dm, B, K, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_import(DevModel* dm, int B, int K, const long long* in, cudaStream_t s)
+{
+    k_moments_import<<<4, 256, 0, s>>>(dm, B, K, in);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pca_moments(const uint16_t* cube, int B, long long P, const uint8_t* mask, DevModel* dm,
                                int num_sms, cudaStream_t s)
