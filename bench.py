@@ -55,6 +55,9 @@ def _args():
     ap.add_argument("--no-precision", action="store_true", help="skip the FP64-form comparison")
     ap.add_argument("--no-forms", action="store_true", help="batch workload: skip the per-page forms")
     ap.add_argument("--pages", type=int, default=64, help="batch workload: number of pages (64 = the benchmark)")
+    ap.add_argument("--split", action="store_true",
+                    help="under torchrun: one page split by rows over the ranks (one all-reduce of the class "
+                         "moments and one of the ranges per step; strong scaling) instead of a page per rank")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other configurations (small page, large cube, 64-page batch) in the line")
     return ap.parse_args()
@@ -1070,8 +1073,70 @@ def run_batch_bench(a):
     print(json.dumps(line), flush=True)
 
 
+def run_split_bench(a):
+    """One page split by rows over the ranks (paper_1612_06457_gb300/split.py):
+    every step each rank finds its band's class moments, the ranks sum them
+    (NCCL all-reduce of int64), finish the same fit, merge the training-score
+    ranges and project their bands.  Wall time per step, bracketed by a
+    barrier and a device synchronization, max over ranks; value = the page's
+    pixels / that time (strong scaling: the work is fixed as N grows)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1612_06457_gb300 as cva
+    from paper_1612_06457_gb300 import split
+
+    world, rank, local = _dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cva.load()
+    w = _workload(a.workload, 0)
+    r0, r1 = split.row_band(w.H, world, rank)
+    cube = torch.from_numpy(np.ascontiguousarray(w.cube[:, r0:r1])).to(dev)
+    labels = torch.from_numpy(np.ascontiguousarray(w.labels[r0:r1])).to(dev)
+    out = torch.empty((w.k, r1 - r0, w.W), dtype=torch.uint8, device=dev)
+    part = split.PagePart(cube, labels, w.K, w.k)
+
+    def step():
+        if world > 1:
+            split.run_split(part, out)
+        else:
+            mom, _ = part.moments()
+            rng, _ = part.fit(mom)
+            part.project(rng, out)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = (time.perf_counter() - t0) * 1e3 / a.steps
+    ms = _max_over_ranks(dist if world > 1 else None, ms, dev)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": w.P / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": world,
+                          "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                          "config": dict(_config(w), parallelism=f"rows split over {world} ranks"),
+                          "timing": "wall clock per step (the protocol synchronizes on the host)"}), flush=True)
+    part.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     a = _args()
+    if a.split and a.impl != "reference":
+        run_split_bench(a)
+        return
     if a.workload == BATCH_WORKLOAD:
         run_batch_bench(a)
     elif a.impl == "reference":

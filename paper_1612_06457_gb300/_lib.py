@@ -47,6 +47,11 @@ SIGNATURES = {
     "cva_set_precision": (_I, [_P, _I]),
     "cva_set_variates": (_I, [_P, _I]),
     "cva_fit": (_I, [_P, _I, _I, _I, _P, _I, _P, _P]),
+    "cva_fit_moments": (_I, [_P, _I, _I, _I, _P, _I, _P, _P]),
+    "cva_model_moments": (_I, [_P, _P, _P]),
+    "cva_fit_from_moments": (_I, [_P, _P, _P]),
+    "cva_model_training_range": (_I, [_P, _P, _P]),
+    "cva_set_training_range": (_I, [_P, _P, _P]),
     "cva_status": (_I, [_P, _P]),
     "cva_model_get": (_I, [_P, _P, _P, _P, _P, _P]),
     "cva_model_get_scatter": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -179,6 +184,49 @@ def cva_fit(cube: torch.Tensor, labels: torch.Tensor, K: int, m: Model, stream=N
     rc = load().cva_fit(_dptr(cube, torch.uint16, "cube"), B, H, W, _dptr(labels, torch.uint8, "labels"),
                         K, m.handle, _stream_ptr(stream))
     _check(rc, "cva_fit")
+
+
+def moment_words(B: int, K: int) -> int:
+    """Words of a class-moment array (CVA_MOMENT_WORDS in cva.h)."""
+    return K * (B + 1) * (B + 2) // 2
+
+
+def cva_fit_moments(cube: torch.Tensor, labels: torch.Tensor, K: int, m: Model, stream=None) -> None:
+    B, H, W = cube.shape
+    if tuple(labels.shape) != (H, W):
+        raise ValueError("labels must be H x W")
+    rc = load().cva_fit_moments(_dptr(cube, torch.uint16, "cube"), B, H, W, _dptr(labels, torch.uint8, "labels"),
+                                K, m.handle, _stream_ptr(stream))
+    _check(rc, "cva_fit_moments")
+
+
+def cva_model_moments(m: Model, moments: torch.Tensor, stream=None) -> None:
+    """Copy the model's class moments into ``moments`` (int64, moment_words(B, K), device)."""
+    if moments.numel() < moment_words(m.B, m.K):
+        raise ValueError("moments must hold moment_words(B, K) int64")
+    _check(load().cva_model_moments(m.handle, _dptr(moments, torch.int64, "moments"), _stream_ptr(stream)),
+           "cva_model_moments")
+
+
+def cva_fit_from_moments(m: Model, moments: torch.Tensor, stream=None) -> None:
+    if moments.numel() < moment_words(m.B, m.K):
+        raise ValueError("moments must hold moment_words(B, K) int64")
+    _check(load().cva_fit_from_moments(m.handle, _dptr(moments, torch.int64, "moments"), _stream_ptr(stream)),
+           "cva_fit_from_moments")
+
+
+def cva_model_training_range(m: Model, range: torch.Tensor, stream=None) -> None:
+    if range.numel() < 2 * m.nvec:
+        raise ValueError("range must hold 2 nvec float32")
+    _check(load().cva_model_training_range(m.handle, _dptr(range, torch.float32, "range"), _stream_ptr(stream)),
+           "cva_model_training_range")
+
+
+def cva_set_training_range(m: Model, range: torch.Tensor, stream=None) -> None:
+    if range.numel() < 2 * m.nvec:
+        raise ValueError("range must hold 2 nvec float32")
+    _check(load().cva_set_training_range(m.handle, _dptr(range, torch.float32, "range"), _stream_ptr(stream)),
+           "cva_set_training_range")
 
 
 def cva_status(m: Model, stream=None) -> int:

@@ -210,6 +210,56 @@ int cva_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, in
     return from_cuda(e);
 }
 
+int cva_fit_moments(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, int K, cva_model* m,
+                    void* stream)
+{
+    if (!m || B != m->B || K != m->K || !valid_dims(B, H, W)) return CVA_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(cube) % 2 != 0) return CVA_ERR_INVALID_ARG;
+    if (!device_visible(cube) || !device_visible(labels)) return CVA_ERR_INVALID_ARG;
+    const long long P = static_cast<long long>(H) * W;
+    const cudaError_t e = cva::launch_fit_moments(cube, B, P, labels, K, m->dm, m->xtr, m->tiles, m->list, m->cap,
+                                                  m->num_sms, static_cast<cudaStream_t>(stream));
+    m->range64_valid = false;
+    m->pca = false;
+    return from_cuda(e);
+}
+
+int cva_model_moments(cva_model* m, int64_t* moments, void* stream)
+{
+    if (!m || !device_visible(moments) || reinterpret_cast<uintptr_t>(moments) % 8 != 0) return CVA_ERR_INVALID_ARG;
+    return from_cuda(cva::launch_moments_export(m->dm, m->B, m->K, reinterpret_cast<long long*>(moments),
+                                                static_cast<cudaStream_t>(stream)));
+}
+
+int cva_fit_from_moments(cva_model* m, const int64_t* moments, void* stream)
+{
+    if (!m || !device_visible(moments) || reinterpret_cast<uintptr_t>(moments) % 8 != 0) return CVA_ERR_INVALID_ARG;
+    if (m->precision != CVA_PRECISION_MIXED) return CVA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cva::launch_moments_import(m->dm, m->B, m->K, reinterpret_cast<const long long*>(moments), s);
+    if (e == cudaSuccess) e = cva::launch_fit_finalize(m->dm, m->B, m->K, m->nvec, s);
+    if (e == cudaSuccess) e = cva::launch_train_range(m->B, m->K, m->xtr, m->dm, m->nvec, m->num_sms, s);
+    m->fit_nvec = m->nvec;
+    m->range64_valid = false;
+    m->pca = false;
+    return from_cuda(e);
+}
+
+int cva_model_training_range(cva_model* m, float* range, void* stream)
+{
+    if (!m || !device_visible(range) || reinterpret_cast<uintptr_t>(range) % 4 != 0) return CVA_ERR_INVALID_ARG;
+    return from_cuda(cudaMemcpyAsync(range, m->dm->train_range, sizeof(float) * 2 * m->fit_nvec,
+                                     cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+}
+
+int cva_set_training_range(cva_model* m, const float* range, void* stream)
+{
+    if (!m || m->pca || !device_visible(range) || reinterpret_cast<uintptr_t>(range) % 4 != 0)
+        return CVA_ERR_INVALID_ARG;
+    return from_cuda(cudaMemcpyAsync(m->dm->train_range, range, sizeof(float) * 2 * m->fit_nvec,
+                                     cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+}
+
 int cva_pca_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* mask, cva_model* m, void* stream)
 {
     if (!m || B != m->B || !valid_dims(B, H, W)) return CVA_ERR_INVALID_ARG;
