@@ -73,9 +73,6 @@ struct DevModel {
     double Sw[MAXB][MAXB];      // within-class scatter
     double Sb[MAXB][MAXB];      // between-class scatter (formed on request from Mb)
     double Mb[MAXB][MAXK];      // sqrt(n_c) (mu_c - mu): Sb = Mb Mb^T
-    double L[MAXB][MAXB];       // lower Cholesky factor of Sw
-    double Linvd[MAXB];         // 1 / L[i][i]
-    double U[MAXB][MAXB];       // whitened eigenvectors, U = L^T V
     double lam[MAXB];           // eigenvalues, descending
     double V[MAXB][MAXB];       // canonical vectors, V[b][j]
 

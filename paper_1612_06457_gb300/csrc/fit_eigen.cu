@@ -86,7 +86,6 @@ constexpr float CLUSTER_REL = 1e-7f;
 
 struct FinSmem {
     df A[MAXB][2 * MAXB + MAXK + 1];  // [Sw | Mb | I] during elimination
-    df L[MAXB][MAXB + 1];
     df G[MAXB][MAXK + 1];
     df Li[MAXB][MAXB + 1];        // L^-1 (lower triangular)
     SymEig<MAXK> eig;             // T = G^T G and its eigen-decomposition
@@ -108,6 +107,9 @@ struct FinSmem {
     unsigned long long N;
     df invN;
     df rnorm;
+    df hv[MAXK];     // Householder vector of the deflation
+    df gv[MAXB];     // G hv
+    df beta;         // 2 / hv^T hv
     float scale;     // power of two bringing T to about unit Frobenius norm
     int fail;
     int r_eff;
@@ -392,9 +394,12 @@ __device__ bool cluster_rotations(SymEig<NM>& e, int n, float delta, float lm)
                     q = df_fma(q, e.W[i][a], e.TW[i][b]);
                     r = df_fma(r, e.W[i][b], e.TW[i][b]);
                 }
-                if (!(fabsf(q.hi) > fmaxf(1e-6f * fabsf(r.hi - p.hi), 1e-12f * lm))) continue;
+                // the diagonal difference and the quotient in double-float: for a
+                // (nearly) degenerate pair r - p is far below FP32 resolution
+                const df d = df_sub(r, p);
+                if (!(fabsf(q.hi) > fmaxf(1e-6f * fabsf(d.hi), 1e-12f * lm))) continue;
                 // rotation J = [[c, s], [-s, c]] with J^T [[p, q], [q, r]] J diagonal
-                const float zeta = (r.hi - p.hi) / (2.0f * q.hi);
+                const float zeta = df_div(d, df_mulf(q, 2.0f)).hi;
                 const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
                 const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = t * c;
                 #pragma unroll 1
@@ -641,33 +646,26 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
     }
     __syncthreads();
     if (tid < B) sm.swd[tid] = sm.A[tid][tid].hi;
-    for (int e = tid; e < MAXB * (MAXB + 1); e += TPB) {
-        (&sm.L[0][0])[e] = df_from(0.0f);
-        (&sm.Li[0][0])[e] = df_from(0.0f);
-    }
+    for (int e = tid; e < MAXB * (MAXB + 1); e += TPB) (&sm.Li[0][0])[e] = df_from(0.0f);
     for (int e = tid; e < B * B; e += TPB) {  // identity columns: the elimination turns them into L^-1
         const int i = e / B, j = e - (e / B) * B;
         sm.A[i][B + K + j] = df_from(i == j ? 1.0f : 0.0f);
     }
     __syncthreads();
 
-    // ---- 2. Cholesky of Sw with [Mb | I] carried along: L, G = L^-1 Mb, L^-1 -
+    // ---- 2. Cholesky of Sw with [Mb | I] carried along: G = L^-1 Mb, L^-1 ----
+    // (L itself is never needed: only the reciprocals of its diagonal)
     if (tid == 0) {
         const df d = sm.A[0][0];
-        if (!(d.hi > static_cast<float>(PIVOT_REL) * sm.swd[0]) || !(d.hi > 0.0f)) {
-            sm.fail = CVA_ERR_NOT_SPD;
-        } else {
-            const df r = df_rsqrt(d);
-            sm.invd[0] = r;
-            sm.L[0][0] = df_mul(d, r);
-        }
+        if (!(d.hi > static_cast<float>(PIVOT_REL) * sm.swd[0]) || !(d.hi > 0.0f)) sm.fail = CVA_ERR_NOT_SPD;
+        else sm.invd[0] = df_rsqrt(d);
     }
     const int KB = K + B;  // carried columns: Mb then the identity
     for (int j = 0; j < B; ++j) {
         __syncthreads();
         if (sm.fail) break;
-        // column j of L, row j of [G | L^-1], and the trailing update, in one
-        // phase: L[i][j] = A[i][j] r and the row-j entries are formed where used.
+        // row j of [G | L^-1] and the trailing update, in one phase: column j
+        // of L, A[i][j] r, is formed where it is used.
         // Item 0 (the next pivot, on the critical path of the elimination) is
         // warp 0's alone, so that no warp runs both paths; the other items are
         // spread over warps 1 .. NWARP-1.
@@ -680,22 +678,17 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
                 const df a = sm.A[j + 1][j];
                 const df v = df_fms(sm.A[j + 1][j + 1], df_mul(a, r), df_mul(a, r));
                 sm.A[j + 1][j + 1] = v;
-                if (!(v.hi > static_cast<float>(PIVOT_REL) * sm.swd[j + 1]) || !(v.hi > 0.0f)) {
-                    sm.fail = CVA_ERR_NOT_SPD;
-                } else {
-                    const df rr = df_rsqrt(v);
-                    sm.invd[j + 1] = rr;
-                    sm.L[j + 1][j + 1] = df_mul(v, rr);
-                }
+                if (!(v.hi > static_cast<float>(PIVOT_REL) * sm.swd[j + 1]) || !(v.hi > 0.0f)) sm.fail = CVA_ERR_NOT_SPD;
+                else sm.invd[j + 1] = df_rsqrt(v);
             }
             continue;
         }
         // item 0 is the pivot's while there is one (m > 0); in the last column it is G[j][0].
-        // Every item is X - (Y r)(Z r) (trailing and carried entries) or Y r (column j
-        // of L, row j of [G | L^-1]); only the operand addresses depend on the kind,
-        // so a warp whose items straddle two kinds diverges only while loading.
+        // Every item is X - (Y r)(Z r) (trailing and carried entries) or Y r (row j
+        // of [G | L^-1]); only the operand addresses depend on the kind, so a warp
+        // whose items straddle two kinds diverges only while loading.
         const float rnc = __frcp_rn(static_cast<float>(ncar));  // (q + 1/2) rnc truncates to q / ncar exactly
-        const int n1 = ntri, n2 = ntri + m * ncar, n3 = n2 + m;
+        const int n1 = ntri, n2 = ntri + m * ncar, n3 = n2;
         for (int e = tid - 32 + (m > 0 ? 1 : 0); e < n3 + ncar; e += TPB - 32) {
             df X = df_from(0.0f), Y, Z = df_from(0.0f);
             df* dst;
@@ -710,11 +703,6 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
                 const int i = j + 1 + qi, col = B + (q - qi * ncar);  // Mb columns, then identity columns 0..j
                 X = sm.A[i][col]; Y = sm.A[i][j]; Z = sm.A[j][col];
                 dst = &sm.A[i][col];
-            } else if (e < n3) {
-                const int i = j + 1 + (e - n2);
-                Y = sm.A[i][j];
-                dst = &sm.L[i][j];
-                fms = false;
             } else {
                 const int cc = e - n3;
                 Y = sm.A[j][B + cc];
@@ -732,30 +720,56 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
         if (tid == 0) set_status(dm, sm.fail);
         return;
     }
-    for (int e = tid; e < B * B; e += TPB) {
-        const int i = e / B, j = e - (e / B) * B;
-        dm->L[i][j] = df_to_double(sm.L[i][j]);
+    // ---- 3. deflation of T's known eigenvalue-0 direction --------------------
+    // G z = 0 for z_c = sqrt(n_c / N) (sum_c n_c (mu_c - mu) = 0), so T = G^T G
+    // has z as an exact eigenvector of eigenvalue 0.  With the Householder
+    // reflection H = I - beta v v^T, v = z + e_{K-1} (H z = -e_{K-1}), the
+    // last column of G H vanishes and its first n = K - 1 columns G' carry all
+    // of T's other eigenpairs: T' = G'^T G' (order K - 1) has them, and
+    // eigenvectors w' of T' give G' w' = G (H w'), the same vectors G w.
+    const int n = K - 1;
+    if (tid < K) {
+        const df z = df_mul(sm.sqn[tid], df_rsqrt(df_from_u64(sm.N)));
+        sm.hv[tid] = (tid == K - 1) ? df_add(z, df_from(1.0f)) : z;
     }
-    if (tid < B) dm->Linvd[tid] = df_to_double(sm.invd[tid]);
+    __syncthreads();
+    if (tid == 0) {
+        df vv = df_from(0.0f);
+        #pragma unroll 1
+        for (int c = 0; c < K; ++c) vv = df_fma(vv, sm.hv[c], sm.hv[c]);
+        sm.beta = df_div(df_from(2.0f), vv);
+    }
+    if (tid < B) {
+        df g = df_from(0.0f);
+        #pragma unroll 1
+        for (int c = 0; c < K; ++c) g = df_fma(g, sm.G[tid][c], sm.hv[c]);
+        sm.gv[tid] = g;
+    }
+    __syncthreads();
+    for (int e = tid; e < B * n; e += TPB) {
+        const int b = e / n, j = e - (e / n) * n;
+        sm.G[b][j] = df_fms(sm.G[b][j], df_mul(sm.beta, sm.gv[b]), sm.hv[j]);
+    }
+    __syncthreads();
 
-    // ---- 3. T = G^T G, scaled by a power of two to about unit norm ----------
+    // ---- 3b. T' = G'^T G', scaled by a power of two to about unit norm -------
     {
-        const int KK = K * K;
+        const int KK = n * n;
         int per = 1;
         while (per * 2 * KK <= TPB && per < 32) per *= 2;
         const int e = tid / per, sub = tid - (tid / per) * per;
         df s = df_from(0.0f);
         if (e < KK) {
-            const int a = e / K, b = e - (e / K) * K;
+            const int a = e / n, b = e - (e / n) * n;
             for (int i = sub; i < B; i += per) s = df_fma(s, sm.G[i][a], sm.G[i][b]);
         }
         for (int o = per / 2; o > 0; o >>= 1) s = df_add(s, shfl_xor_df(s, o));
-        if (e < KK && sub == 0) sm.eig.T[e / K][e % K] = s;
+        if (e < KK && sub == 0) sm.eig.T[e / n][e % n] = s;
     }
     __syncthreads();
     if (tid < 32) {
         float f = 0.0f;
-        for (int e = tid; e < K * K; e += 32) f = fmaf(sm.eig.T[e / K][e % K].hi, sm.eig.T[e / K][e % K].hi, f);
+        for (int e = tid; e < n * n; e += 32) f = fmaf(sm.eig.T[e / n][e % n].hi, sm.eig.T[e / n][e % n].hi, f);
         f = warp_sumf(f);
         if (tid == 0) {
             int ex = 0;
@@ -765,17 +779,26 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
     }
     __syncthreads();
     const float scale = sm.scale;
-    if (tid < K * K) {
-        const int a = tid / K, b = tid % K;
+    if (tid < n * n) {
+        const int a = tid / n, b = tid % n;
         sm.eig.T[a][b] = df_mulf(sm.eig.T[a][b], scale);  // exact: a power of two
         sm.eig.Tf[a][b] = sm.eig.T[a][b].hi;
         sm.eig.Wf[a][b] = (a == b) ? 1.0f : 0.0f;
     }
     __syncthreads();
 
-    // ---- 4. FP32 cyclic Jacobi on T, then 5. refinement ----------------------
-    sym_eig<MAXK>(sm.eig, K, true);
-    __syncthreads();
+    // ---- 4. FP32 cyclic Jacobi on T', then 5. refinement ---------------------
+    if (n == 1) {  // two classes: T' is 1 x 1
+        if (tid == 0) {
+            sm.eig.W[0][0] = df_from(1.0f);
+            sm.eig.lam[0] = sm.eig.T[0][0];
+            sm.eig.last_correction = 0.0f;
+        }
+        __syncthreads();
+    } else {
+        sym_eig<MAXK>(sm.eig, n, true);
+        __syncthreads();
+    }
     if (!(sm.eig.last_correction < REFINE_DONE)) {
         if (tid == 0) set_status(dm, CVA_ERR_NO_CONVERGENCE);
         return;
@@ -784,9 +807,9 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
     // ---- 6. eigenvalues in descending order, whitened eigenvectors ----------
     if (tid == 0) {
         int used = 0;
-        for (int j = 0; j < K; ++j) {
+        for (int j = 0; j < n; ++j) {
             int best = -1;
-            for (int i = 0; i < K; ++i) {
+            for (int i = 0; i < n; ++i) {
                 if (used & (1 << i)) continue;
                 if (best < 0 || df_gt(sm.eig.lam[i], sm.eig.lam[best])) best = i;
             }
@@ -812,7 +835,7 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
         const int w = sm.order[j];
         df s = df_from(0.0f);
         #pragma unroll 1
-        for (int c = 0; c < K; ++c) s = df_fma(s, sm.G[b][c], sm.eig.W[c][w]);
+        for (int c = 0; c < n; ++c) s = df_fma(s, sm.G[b][c], sm.eig.W[c][w]);
         sm.U[b][j] = s;
     }
     __syncthreads();
@@ -880,7 +903,6 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
         const int b = e / MAXB, j = e - (e / MAXB) * MAXB;
         const bool live = b < B && j < ncols;
         dm->V[b][j] = live ? df_to_double(sm.V[b][j]) : 0.0;
-        dm->U[b][j] = live ? df_to_double(sm.U[b][j]) : 0.0;
         dm->Vf[b][j] = live ? sm.V[b][j].hi : 0.0f;
     }
     if (tid < MAXB) {
@@ -1041,7 +1063,6 @@ __global__ void __launch_bounds__(TPB) k_pca_finalize(DevModel* __restrict__ dm,
         const bool live = b < B && j < ncols;
         const double v = live ? df_to_double(sm.V[b][j]) : 0.0;
         dm->V[b][j] = v;
-        dm->U[b][j] = v;
         dm->Vf[b][j] = live ? sm.V[b][j].hi : 0.0f;
     }
     for (int q = tid; q < MAXB * MAXK; q += TPB) dm->Mb[q / MAXK][q % MAXK] = 0.0;
