@@ -878,6 +878,227 @@ __global__ void k_moments_import(DevModel* __restrict__ dm, int B, int K, const 
     if (blockIdx.x == 0 && threadIdx.x == 0) dm->fitted = 0;
 }
 
+// ---------------------------------------------------------------------------
+// Principal components, register form (B + 1 <= 24 augmented bands, P % 8 ==
+// 0, 16-byte aligned cube, 8-byte aligned mask).  Each warp takes a
+// contiguous range of pixels and forms the Gram matrix of the byte-split
+// augmented vectors X = [h ; l] (2F rows: the high bytes of bands 0..F-1,
+// then the low bytes; row B is the "1" of the augmented vector) with
+// mma.sync m16n8k16 f16 x f16 -> f32, straight from its loads:
+//   * the Gram matrix sums over pixels, so which pixel feeds which k slot of
+//     an mma is free; lane (g, t) = (lane / 4, lane % 4) takes 8 consecutive
+//     pixels of every 32 from one 16-byte load per band and feeds them to the
+//     k slots it owns in the A fragment, and the B fragment of column group j
+//     (columns = rows of X) is the A fragment's registers of row group j;
+//   * lane g holds bands g, g + 8, g + 16 of each pixel: one 16-byte load per
+//     band and 32 pixels, 64 contiguous bytes for the 4 lanes of a band;
+//   * a byte v becomes the f16 value v exactly by one byte permute (the f16
+//     bits of 1024 + v are 0x64 : v) and one packed f16 subtraction of 1024;
+//   * each product is at most 255^2, so an FP32 accumulator stays an exact
+//     integer (below 2^24) for 256 pixels; the warp drains its accumulators
+//     into 32-bit integer sums every 256 pixels and into shared memory every
+//     32768 (the 32-bit sums stay below 2^32), so no block barrier is taken
+//     while pixels stream;
+//   * at the end the CTA's 64-bit sums in shared memory are recombined into
+//     moments, M = 65536 C_hh + 256 (C_hl + C_lh) + C_ll, and added to the
+//     model with one atomic per moment.
+// Only Gram tiles on or above the diagonal are formed: 12 mma per 16 pixels
+// at F = 24.
+// ---------------------------------------------------------------------------
+namespace pcar {
+
+constexpr int TPBR = 384;             // 12 warps, one CTA an SM
+constexpr int DSTEP = 32;             // pixels of one double step (two mma k steps)
+constexpr int DRAIN = 8;              // double steps between drains (256 pixels)
+constexpr int FLUSH = 1024;           // double steps between flushes to shared memory (32768 pixels)
+
+__device__ __forceinline__ void mma_f16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                              uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// f16x2 of the low (hi = false) or high bytes of the two 16-bit values in w,
+// exactly: the permute builds the f16 bit patterns of 1024 + byte, the
+// packed subtraction removes 1024.
+__device__ __forceinline__ uint32_t bytes_to_f16x2(uint32_t w, bool hi)
+{
+    const uint32_t biased = __byte_perm(w, 0x64646464u, hi ? 0x4341u : 0x4240u);
+    uint32_t r;
+    asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(r) : "r"(biased), "r"(0x64006400u));
+    return r;
+}
+
+// Number of Gram tiles (16-row block R, 8-column group C) on or above the
+// diagonal: C >= 2 R.
+__host__ __device__ constexpr int ntiles(int F)
+{
+    return (2 * F / 16) * (2 * F / 8) - (2 * F / 16) * (2 * F / 16 - 1);
+}
+
+// The lane's 16-byte loads of one double step: bands g + 8 i < B from the
+// cube, the "1" of the augmented vector as the value 1 at every pixel (its
+// high byte 0, its low byte 1), padding bands 0; lanes past the warp's range
+// load zeros.  With a mask, the values of pixels outside it become 0 (the
+// "1" included), so they add nothing.
+template <int NBL, bool MASKED>
+__device__ __forceinline__ void load_dstep(const uint16_t* __restrict__ cube, const uint8_t* __restrict__ mask, int B,
+                                           long long P, long long p, long long p_end, int g, uint4 (&v)[NBL])
+{
+    const bool in = p < p_end;
+    #pragma unroll
+    for (int i = 0; i < NBL; ++i) {
+        const int band = g + 8 * i;
+        v[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (in && band < B) v[i] = __ldcs(reinterpret_cast<const uint4*>(cube + static_cast<long long>(band) * P + p));
+        else if (in && band == B) v[i] = make_uint4(0x00010001u, 0x00010001u, 0x00010001u, 0x00010001u);
+    }
+    if (MASKED && in) {
+        const uint2 mv = *reinterpret_cast<const uint2*>(mask + p);
+        // keep-mask of the two 16-bit values of word w (mask bytes 2 w, 2 w + 1)
+        uint32_t keep[4];
+        #pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint32_t m = w < 2 ? mv.x : mv.y;
+            const int j = 2 * (w & 1);
+            keep[w] = (((m >> (8 * j)) & 0xFFu) ? 0x0000FFFFu : 0u) | (((m >> (8 * (j + 1))) & 0xFFu) ? 0xFFFF0000u : 0u);
+        }
+        #pragma unroll
+        for (int i = 0; i < NBL; ++i) {
+            v[i].x &= keep[0];
+            v[i].y &= keep[1];
+            v[i].z &= keep[2];
+            v[i].w &= keep[3];
+        }
+    }
+}
+
+// Dynamic shared memory of k_pca_moments_reg<F>: the CTA's 64-bit Gram sums
+// (2F x 2F) and every lane's 32-bit partial sums (NT x 4 a lane).
+__host__ __device__ constexpr size_t reg_smem_bytes(int F)
+{
+    return static_cast<size_t>(2 * F) * (2 * F) * 8 + static_cast<size_t>(TPBR / 32) * ntiles(F) * 4 * 32 * 4;
+}
+
+template <int F, bool MASKED>
+__global__ void __launch_bounds__(pcar::TPBR, 1)
+k_pca_moments_reg(const uint16_t* __restrict__ cube, int B, long long P, const uint8_t* __restrict__ mask,
+                  long long chunk, DevModel* __restrict__ dm)
+{
+    constexpr int NBL = F / 8;              // bands per lane
+    constexpr int RB = 2 * F / 16;          // 16-row blocks of the Gram matrix
+    constexpr int CG = 2 * F / 8;           // 8-column groups
+    constexpr int NT = pcar::ntiles(F);
+    constexpr int D = 4;                    // double steps in the load ring (three ahead)
+    extern __shared__ __align__(16) unsigned char rdyn[];
+    unsigned long long (*S)[2 * F] = reinterpret_cast<unsigned long long (*)[2 * F]>(rdyn);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    // this lane's 32-bit sums: entry (q, e) at SS[(q * 4 + e) * 32 + lane] (one bank a lane)
+    uint32_t* SS = reinterpret_cast<uint32_t*>(rdyn + static_cast<size_t>(2 * F) * (2 * F) * 8) +
+                   static_cast<size_t>(warp) * NT * 4 * 32;
+    for (int i = tid; i < 4 * F * F; i += pcar::TPBR) (&S[0][0])[i] = 0ull;
+    for (int i = lane; i < NT * 4 * 32; i += 32) SS[i] = 0u;
+    __syncthreads();
+
+    const long long wid = (static_cast<long long>(blockIdx.x) * pcar::TPBR + tid) >> 5;
+    const long long p_begin = wid * chunk;
+    const long long p_end = min(P, p_begin + chunk);
+    float acc[NT][4];
+    #pragma unroll
+    for (int q = 0; q < NT; ++q)
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) acc[q][e] = 0.0f;
+
+    // FP32 accumulators (exact integers below 2^24) into the 32-bit sums
+    auto drain = [&]() {
+        #pragma unroll
+        for (int q = 0; q < NT; ++q)
+            #pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                SS[(q * 4 + e) * 32 + lane] += __float2uint_rn(acc[q][e]);
+                acc[q][e] = 0.0f;
+            }
+    };
+    // 32-bit sums into the CTA's 64-bit sums; entry e of tile q of this lane
+    // is row 16 R + g + 8 (e >> 1), column 8 C + 2 t + (e & 1)
+    auto flush = [&]() {
+        int q = 0;
+        #pragma unroll
+        for (int R = 0; R < RB; ++R)
+            #pragma unroll
+            for (int C = 2 * R; C < CG; ++C, ++q)
+                #pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int row = 16 * R + g + 8 * (e >> 1), col = 8 * C + 2 * t + (e & 1);
+                    uint32_t& v = SS[(q * 4 + e) * 32 + lane];
+                    if (row <= col && v) atomicAdd(&S[row][col], static_cast<unsigned long long>(v));
+                    v = 0u;
+                }
+    };
+    auto compute = [&](const uint4 (&cur)[NBL]) {
+        #pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            // this k step: pixels 4 k .. 4 k + 3 of the lane's eight
+            uint32_t X[2 * NBL][2];
+            #pragma unroll
+            for (int i = 0; i < NBL; ++i) {
+                const uint32_t w0 = k ? cur[i].z : cur[i].x, w1 = k ? cur[i].w : cur[i].y;
+                X[i][0] = pcar::bytes_to_f16x2(w0, true);
+                X[i][1] = pcar::bytes_to_f16x2(w1, true);
+                X[NBL + i][0] = pcar::bytes_to_f16x2(w0, false);
+                X[NBL + i][1] = pcar::bytes_to_f16x2(w1, false);
+            }
+            int q = 0;
+            #pragma unroll
+            for (int R = 0; R < RB; ++R)
+                #pragma unroll
+                for (int C = 2 * R; C < CG; ++C, ++q)
+                    pcar::mma_f16_16816(acc[q], X[2 * R][0], X[2 * R + 1][0], X[2 * R][1], X[2 * R + 1][1],
+                                        X[C][0], X[C][1]);
+        }
+    };
+
+    if (p_begin < p_end) {
+        uint4 buf[D][NBL];
+        #pragma unroll
+        for (int j = 0; j < D - 1; ++j)
+            load_dstep<NBL, MASKED>(cube, mask, B, P, p_begin + j * pcar::DSTEP + 8 * t, p_end, g, buf[j]);
+        int rounds = 0;  // outer rounds of D double steps
+        for (long long dp = p_begin; dp < p_end; dp += D * pcar::DSTEP) {
+            #pragma unroll
+            for (int j = 0; j < D; ++j) {
+                // double steps past p_end load zeros and add nothing
+                load_dstep<NBL, MASKED>(cube, mask, B, P, dp + (j + D - 1) * pcar::DSTEP + 8 * t, p_end, g,
+                                        buf[(j + D - 1) % D]);
+                compute(buf[j]);
+            }
+            ++rounds;
+            if ((rounds * D) % pcar::DRAIN == 0) {
+                drain();
+                if ((rounds * D) % pcar::FLUSH == 0) flush();
+            }
+        }
+        drain();
+        flush();
+    }
+    __syncthreads();
+    // moments of the augmented vectors: M[a][b] = 65536 hh + 256 (hl + lh) + ll
+    const int BA = B + 1, nb = mom_shape(B).nb;
+    for (int q = tid; q < BA * (BA + 1) / 2; q += pcar::TPBR) {
+        int a = 0, r = q;
+        while (r >= BA - a) { r -= BA - a; ++a; }
+        const int b = a + r;
+        const unsigned long long M = (S[a][b] << 16) + ((S[a][F + b] + S[b][F + a]) << 8) + S[F + a][F + b];
+        if (M) atomicAdd(&dm->mom[0][blk_index(a >> 2, b >> 2, nb)][(a & 3) * 4 + (b & 3)], M);
+    }
+}
+
+}  // namespace pcar
+
 // Clears class 0's moments and the fit state before a principal-component fit.
 __global__ void k_pca_reset(DevModel* __restrict__ dm, int B)
 {
@@ -985,6 +1206,34 @@ cudaError_t launch_pca_moments(const uint16_t* cube, int B, long long P, const u
     k_pca_reset<<<1, 256, 0, s>>>(dm, B);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    const int F = xtr_row(B);
+    const bool reg = F <= 24 && P % 8 == 0 && reinterpret_cast<uintptr_t>(cube) % 16 == 0 &&
+                     (!mask || reinterpret_cast<uintptr_t>(mask) % 8 == 0);
+    if (reg) {
+        // one CTA of 12 warps an SM, each warp a contiguous run of pixels
+        // (a multiple of 32, at least 256)
+        const long long warps = static_cast<long long>(num_sms) * (pcar::TPBR / 32);
+        long long chunk = (P + warps - 1) / warps;
+        chunk = ((chunk + pcar::DSTEP - 1) / pcar::DSTEP) * pcar::DSTEP;
+        if (chunk < 256) chunk = 256;
+        const long long nw = (P + chunk - 1) / chunk;
+        const unsigned grid = static_cast<unsigned>((nw + pcar::TPBR / 32 - 1) / (pcar::TPBR / 32));
+        const size_t sm = pcar::reg_smem_bytes(F);
+        auto go = [&](auto kern) -> cudaError_t {
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+            if (e2 != cudaSuccess) return e2;
+            kern<<<grid, pcar::TPBR, sm, s>>>(cube, B, P, mask, chunk, dm);
+            return cudaGetLastError();
+        };
+        if (mask) {
+            if (F == 8) return go(pcar::k_pca_moments_reg<8, true>);
+            if (F == 16) return go(pcar::k_pca_moments_reg<16, true>);
+            return go(pcar::k_pca_moments_reg<24, true>);
+        }
+        if (F == 8) return go(pcar::k_pca_moments_reg<8, false>);
+        if (F == 16) return go(pcar::k_pca_moments_reg<16, false>);
+        return go(pcar::k_pca_moments_reg<24, false>);
+    }
     const long long units = (P + UNIT - 1) / UNIT;
     long long grid = static_cast<long long>(num_sms) * 6;
     if (grid > units) grid = units;
