@@ -387,8 +387,15 @@ void cva_batch_destroy(cva_batch* b);
  * workspace must not overlap on the GPU. */
 int cva_fit_project_batched(cva_batch* b, const cva_page* pages, int n, void* stream);
 
+/* The fit alone: every page's fit and training-score range, no projection
+ * (cva_project_batched then projects).  Splitting the two lets a caller run
+ * the projection of one batch while the next batch is fitted, e.g. the fits
+ * on a high-priority stream and the projections on a low-priority one.
+ * Asynchronous; allocates nothing. */
+int cva_fit_batched(cva_batch* b, const cva_page* pages, int n, void* stream);
+
 /* The projection pass alone: project every page again with the models of
- * the last cva_fit_project_batched on this workspace, which must have been
+ * the last cva_fit_project_batched (or cva_fit_batched) on this workspace, which must have been
  * given the same pages in the same order (same shapes and classes; the cube
  * contents may differ, e.g. the same pages imaged again).  Asynchronous;
  * allocates nothing. */

@@ -69,6 +69,7 @@ SIGNATURES = {
     "cva_fit_project_batched": (_I, [_P, _P, _I, _P]),
     "cva_batch_status": (_I, [_P, _I, _P, _P]),
     "cva_project_batched": (_I, [_P, _P, _I, _P]),
+    "cva_fit_batched": (_I, [_P, _P, _I, _P]),
     "cva_batch_tune": (_I, [_P, _P, _I, _P, _P]),
     "cva_strerror": (ctypes.c_char_p, [_I]),
 }
@@ -369,6 +370,12 @@ def cva_fit_project_batched(b: Batch, pages, stream=None) -> None:
     ``pages``: sequence of (cube, labels, K, k, out[, eigvals]) device tensors."""
     arr = _pages(pages)
     _check(load().cva_fit_project_batched(b.handle, arr, len(pages), _stream_ptr(stream)), "cva_fit_project_batched")
+
+
+def cva_fit_batched(b: Batch, pages, stream=None) -> None:
+    """Every page's fit alone (no projection); cva_project_batched projects."""
+    arr = _pages(pages)
+    _check(load().cva_fit_batched(b.handle, arr, len(pages), _stream_ptr(stream)), "cva_fit_batched")
 
 
 def cva_project_batched(b: Batch, pages, stream=None) -> None:

@@ -356,7 +356,7 @@ cudaError_t launch_projection(cva_batch* b, int n, const Plan& plan, cudaStream_
     return e;
 }
 
-cudaError_t run_batch(cva_batch* b, int n, const Plan& plan, cudaStream_t s)
+cudaError_t run_batch(cva_batch* b, int n, const Plan& plan, cudaStream_t s, bool project = true)
 {
     cudaError_t e = upload_pages(b, n, s);
     if (e == cudaSuccess) e = cva::launch_batch_tile_count(b->pages, b->tile_page, plan.tiles_total, s);
@@ -371,7 +371,7 @@ cudaError_t run_batch(cva_batch* b, int n, const Plan& plan, cudaStream_t s)
     if (e == cudaSuccess) e = cva::launch_batch_finalize(b->pages, n, s);
     if (e == cudaSuccess)
         e = cva::launch_batch_train_range(b->pages, n, b->tot, b->xtr, plan.max_k, b->num_sms, s);
-    if (e == cudaSuccess) e = launch_projection(b, n, plan, s);
+    if (e == cudaSuccess && project) e = launch_projection(b, n, plan, s);
     return e;
 }
 
@@ -441,6 +441,14 @@ int cva_fit_project_batched(cva_batch* b, const cva_page* pages, int n, void* st
     const int rc = plan_batch(b, pages, n, &plan);
     if (rc != CVA_OK) return rc;
     return run_batch(b, n, plan, static_cast<cudaStream_t>(stream)) == cudaSuccess ? CVA_OK : CVA_ERR_CUDA;
+}
+
+int cva_fit_batched(cva_batch* b, const cva_page* pages, int n, void* stream)
+{
+    Plan plan;
+    const int rc = plan_batch(b, pages, n, &plan);
+    if (rc != CVA_OK) return rc;
+    return run_batch(b, n, plan, static_cast<cudaStream_t>(stream), false) == cudaSuccess ? CVA_OK : CVA_ERR_CUDA;
 }
 
 int cva_project_batched(cva_batch* b, const cva_page* pages, int n, void* stream)

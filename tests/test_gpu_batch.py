@@ -208,3 +208,28 @@ def test_batch64_at_full_size_against_oracle_and_single_page_path():
         assert (d <= 1).mean() >= 0.999, i
     b.close()
 
+
+
+def test_fit_alone_then_projection_equals_the_whole_batch_call():
+    """cva_fit_batched (every page's fit, no projection) followed by
+    cva_project_batched gives the images of cva_fit_project_batched."""
+    _skip_without_gpu()
+    ws = batch_workloads(count=5, seed0=7600, sizes=[256, 384])
+    pages = _pages(ws)
+    b = cva.Batch(len(ws), sum(w.P for w in ws), 500_000)
+    cva.cva_fit_project_batched(b, pages)
+    ref = [p[4].cpu().numpy() for p in pages]
+    lam_ref = [p[5].cpu().numpy() for p in pages]
+    for p in pages:
+        p[4].fill_(7)
+        p[5].fill_(0.0)
+    cva.cva_fit_batched(b, pages)
+    torch.cuda.synchronize()
+    assert all(int((p[4] != 7).sum().item()) == 0 for p in pages)   # nothing projected yet
+    assert (cva.cva_batch_status(b, len(ws)) == cva.CVA_OK).all()
+    cva.cva_project_batched(b, pages)
+    torch.cuda.synchronize()
+    for p, u, lam in zip(pages, ref, lam_ref):
+        np.testing.assert_array_equal(p[4].cpu().numpy(), u)
+        np.testing.assert_array_equal(p[5].cpu().numpy(), lam)
+    b.close()
