@@ -92,10 +92,10 @@ typedef struct cva_model cva_model;
 
 /* Create a model for B bands and K classes on the current CUDA device.  Owns
  * until cva_model_destroy: a device block of about 150 KB, a 512 KB
- * histogram block for cva_percentile_range, a per-tile
- * workspace of 0.5 MB per class, and the gathered training matrix of
- * 2 ((B + 8) & ~7) bytes per training pixel with room for
- * CVA_DEFAULT_TRAIN_CAPACITY pixels (see cva_model_reserve).  *out is set to
+ * histogram block for cva_percentile_range, and, with room for
+ * CVA_DEFAULT_TRAIN_CAPACITY training pixels (see cva_model_reserve), the
+ * gathered training matrix of 2 ((B + 8) & ~7) bytes per training pixel and
+ * a training-pixel index list of 4 K bytes per training pixel.  *out is set to
  * NULL on error.  Not stream-ordered: allocates with cudaMalloc, so call it
  * outside stream capture. */
 #define CVA_DEFAULT_TRAIN_CAPACITY (1 << 22)
@@ -324,7 +324,7 @@ int cva_project_u8(const uint16_t* cube, int B, int H, int W, cva_model* m, int 
  * loops that must never enter the driver's allocator).
  * Does what cva_fit followed by cva_project_u8 with CVA_RANGE_TRAINING does
  * (the same kernels), forming k canonical vectors.  All scratch memory (about
- * 22 MB) is one array in the library's device data, which every GPU that
+ * 38 MB) is one array in the library's device data, which every GPU that
  * loads the library holds until the process exits.
  *   cube, labels  device, as for cva_fit
  *   k             variates to project, 1 <= k <= B

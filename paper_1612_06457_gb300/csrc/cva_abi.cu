@@ -20,8 +20,7 @@ struct cva_model {
     bool range64_valid;  // dm->train_enc64 belongs to the last fit
     bool pca;            // the last fit was a principal-component fit (no training range)
     cva::DevModel* dm;
-    unsigned int* tiles; // per-tile class counts, then first rows (MAX_TILES x (K + 1))
-    unsigned int* list;  // class-major training-pixel indices, cap entries
+    unsigned int* list;  // training-pixel indices, K class regions of cap entries
     uint16_t* xtr;       // gathered training matrix, cap rows of xtr_row(B)
     long long cap;       // training pixels `list` and `xtr` hold
     unsigned int* hist;  // order-statistic histograms, MAXB x 2 x 2048 words (zero between calls)
@@ -99,19 +98,16 @@ int cva_model_create(int B, int K, cva_model** out)
     if (cudaGetDevice(&dev) != cudaSuccess) return CVA_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CVA_ERR_CUDA;
     DevModel* dm = nullptr;
-    unsigned int* tiles = nullptr;
     unsigned int* list = nullptr;
     uint16_t* xtr = nullptr;
     unsigned int* hist = nullptr;
     const size_t cap = CVA_DEFAULT_TRAIN_CAPACITY;
     if (cudaMalloc(&dm, sizeof(DevModel)) != cudaSuccess) return CVA_ERR_CUDA;
-    if (cudaMalloc(&tiles, sizeof(unsigned int) * static_cast<size_t>(cva::MAX_TILES) * (K + 1)) != cudaSuccess ||
-        cudaMalloc(&list, sizeof(unsigned int) * cap) != cudaSuccess ||
+    if (cudaMalloc(&list, sizeof(unsigned int) * cap * static_cast<size_t>(K)) != cudaSuccess ||
         cudaMalloc(&xtr, sizeof(uint16_t) * cap * cva::xtr_row(B)) != cudaSuccess ||
         cudaMalloc(&hist, sizeof(unsigned int) * HIST_WORDS) != cudaSuccess ||
         cudaMemset(dm, 0, sizeof(DevModel)) != cudaSuccess || cudaMemset(hist, 0, sizeof(unsigned int) * HIST_WORDS)) {
         cudaFree(dm);
-        cudaFree(tiles);
         cudaFree(list);
         cudaFree(xtr);
         cudaFree(hist);
@@ -120,7 +116,6 @@ int cva_model_create(int B, int K, cva_model** out)
     cva_model* m = new (std::nothrow) cva_model;
     if (!m) {
         cudaFree(dm);
-        cudaFree(tiles);
         cudaFree(list);
         cudaFree(xtr);
         cudaFree(hist);
@@ -136,7 +131,6 @@ int cva_model_create(int B, int K, cva_model** out)
     m->range64_valid = false;
     m->pca = false;
     m->dm = dm;
-    m->tiles = tiles;
     m->list = list;
     m->xtr = xtr;
     m->hist = hist;
@@ -152,7 +146,8 @@ int cva_model_reserve(cva_model* m, int64_t max_train)
     if (cudaDeviceSynchronize() != cudaSuccess) return CVA_ERR_CUDA;
     unsigned int* list = nullptr;
     uint16_t* xtr = nullptr;
-    if (cudaMalloc(&list, sizeof(unsigned int) * static_cast<size_t>(max_train)) != cudaSuccess) return CVA_ERR_CUDA;
+    if (cudaMalloc(&list, sizeof(unsigned int) * static_cast<size_t>(max_train) * m->K) != cudaSuccess)
+        return CVA_ERR_CUDA;
     if (cudaMalloc(&xtr, sizeof(uint16_t) * static_cast<size_t>(max_train) * cva::xtr_row(m->B)) != cudaSuccess) {
         cudaFree(list);
         return CVA_ERR_CUDA;
@@ -170,7 +165,6 @@ void cva_model_destroy(cva_model* m)
     if (!m) return;
     cudaDeviceSynchronize();
     cudaFree(m->dm);
-    cudaFree(m->tiles);
     cudaFree(m->list);
     cudaFree(m->xtr);
     cudaFree(m->hist);
@@ -200,7 +194,7 @@ int cva_fit(const uint16_t* cube, int B, int H, int W, const uint8_t* labels, in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long P = static_cast<long long>(H) * W;
     cudaError_t e =
-        cva::launch_fit_moments(cube, B, P, labels, K, m->dm, m->xtr, m->tiles, m->list, m->cap, m->num_sms, s);
+        cva::launch_fit_moments(cube, B, P, labels, K, m->dm, m->xtr, m->list, m->cap, m->num_sms, s);
     if (e == cudaSuccess) e = cva::launch_fit_finalize(m->dm, B, K, m->nvec, s);
     if (e == cudaSuccess) e = cva::launch_train_range(B, K, m->xtr, m->dm, m->nvec, m->num_sms, s);
     m->fit_nvec = m->nvec;
@@ -217,7 +211,7 @@ int cva_fit_moments(const uint16_t* cube, int B, int H, int W, const uint8_t* la
     if (reinterpret_cast<uintptr_t>(cube) % 2 != 0) return CVA_ERR_INVALID_ARG;
     if (!device_visible(cube) || !device_visible(labels)) return CVA_ERR_INVALID_ARG;
     const long long P = static_cast<long long>(H) * W;
-    const cudaError_t e = cva::launch_fit_moments(cube, B, P, labels, K, m->dm, m->xtr, m->tiles, m->list, m->cap,
+    const cudaError_t e = cva::launch_fit_moments(cube, B, P, labels, K, m->dm, m->xtr, m->list, m->cap,
                                                   m->num_sms, static_cast<cudaStream_t>(stream));
     m->range64_valid = false;
     m->pca = false;

@@ -117,13 +117,12 @@ __host__ __device__ inline int xtr_row(int B)
     return (B + 1 + 7) & ~7;
 }
 
-// Training-pixel passes: per-tile class counts (`tiles`: ceil(P / LABEL_TILE)
-// rows of K + 1 words) and their prefix sums, the class-major pixel list
-// (`list`, `cap` entries), the gather of every training pixel's bands into
-// the class-major matrix `xtr` (`cap` rows of xtr_row(B)), then the exact
-// moments from it.
+// Training-pixel passes: a reset, one pass over the labels writing every
+// training pixel's index to its class's region of `list` (K regions of `cap`
+// entries), the gather of every training pixel's bands into the class-major
+// matrix `xtr` (`cap` rows of xtr_row(B)), then the exact moments from it.
 cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const uint8_t* labels,
-                               int K, DevModel* dm, uint16_t* xtr, unsigned int* tiles, unsigned int* list,
+                               int K, DevModel* dm, uint16_t* xtr, unsigned int* list,
                                long long cap, int num_sms, cudaStream_t s);
 cudaError_t launch_fit_finalize(DevModel* dm, int B, int K, int nvec, cudaStream_t s);
 // The class moments as K x (B+1)(B+2)/2 int64 words (class-major, upper

@@ -273,13 +273,6 @@ __device__ __forceinline__ void tile_count_body(const uint8_t* __restrict__ labe
     scan_tiles(ntiles, K, B, cap, tiles, dm);
 }
 
-__global__ void __launch_bounds__(TPB)
-k_tile_count(const uint8_t* __restrict__ labels, long long P, int K, int B, int vec, long long cap, int ntiles,
-             unsigned int* __restrict__ tiles, DevModel* __restrict__ dm)
-{
-    tile_count_body(labels, P, K, B, vec, cap, ntiles, tiles, dm, blockIdx.x);
-}
-
 // Adds k to the 16-bit class counter c of packed counters v.
 __device__ inline void bump_by(unsigned long long (&v)[4], int c, unsigned int k)
 {
@@ -335,15 +328,6 @@ __device__ __forceinline__ void tile_compact_body(const uint8_t* __restrict__ la
     }
 }
 
-__global__ void __launch_bounds__(TPB)
-k_tile_compact(const uint8_t* __restrict__ labels, long long P, int K, int vec,
-               const unsigned int* __restrict__ tiles, unsigned int* __restrict__ list,
-               const DevModel* __restrict__ dm)
-{
-    if (dm->status != 0) return;
-    tile_compact_body(labels, P, K, vec, tiles, dm->cls_count, list, blockIdx.x);
-}
-
 // A read-only 16-bit load that asks L2 to fetch 64 bytes around it: the
 // training pixels sit in short runs (4-23 pixels on average per class on the
 // benchmark page), so the default fetches mostly bring unused bytes; measured
@@ -359,12 +343,11 @@ __device__ inline uint32_t ld_u16_l2_64(const uint16_t* p)
 
 // The augmented row (x_0 .. x_{B-1}, 1, 0 ..) of listed training pixel i,
 // all its band loads in flight, stored as one 16-byte-aligned row.
-__device__ __forceinline__ void gather_row(const uint16_t* __restrict__ cube, int B, long long P,
-                                           const unsigned int* __restrict__ list, uint16_t* __restrict__ xtr,
-                                           unsigned int i)
+__device__ __forceinline__ void gather_row(const uint16_t* __restrict__ cube, int B, long long P, unsigned int pix,
+                                           uint16_t* __restrict__ xtr, unsigned int i)
 {
     const int BR = xtr_row(B);
-    const uint16_t* src = cube + list[i];
+    const uint16_t* src = cube + pix;
     uint32_t xv[MAXB];
     #pragma unroll
     for (int b = 0; b < MAXB; ++b) xv[b] = (b < B) ? ld_u16_l2_64(src + static_cast<long long>(b) * P) : 0u;
@@ -385,16 +368,114 @@ __device__ __forceinline__ void gather_row(const uint16_t* __restrict__ cube, in
     }
 }
 
-// One thread per listed training pixel: the class-major training matrix.
+// The fit's state before the label scan: moments and class counters zero,
+// status clear, model not fitted (one CTA).
+__global__ void k_fit_reset(DevModel* __restrict__ dm, int B, int K)
+{
+    const MomShape sh = mom_shape(B);
+    for (int i = threadIdx.x; i < K * sh.nblk * 16; i += blockDim.x) {
+        const int c = i / (sh.nblk * 16), rest = i - c * sh.nblk * 16;
+        dm->mom[c][rest >> 4][rest & 15] = 0ull;
+    }
+    if (threadIdx.x < MAXK) dm->cls_count[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) {
+        dm->status = CVA_OK;
+        dm->fitted = 0;
+    }
+}
+
+// One pass over the labels: the index of every training pixel goes to its
+// class's region of the list (class c at list + c cap, in no particular
+// order).  Each warp takes 512 labels at a time (16 a lane, one 16-byte
+// load) and skips them when none is set; for each class present in them a
+// warp prefix sum of the lanes' counts and one atomic on the class counter
+// give every lane its rows.  The moments are exact integer sums and the
+// ranges minima and maxima, so nothing downstream depends on the order.
+// A label above K sets CVA_ERR_LABEL_RANGE; entries beyond cap are dropped
+// (the gather then reports CVA_ERR_CAPACITY).
+__global__ void __launch_bounds__(TPB)
+k_label_scan(const uint8_t* __restrict__ labels, long long P, int K, int vec, long long cap,
+             unsigned int* __restrict__ list, DevModel* __restrict__ dm)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nchunk = (P + 511) / 512;
+    const long long wid = (static_cast<long long>(blockIdx.x) * TPB + threadIdx.x) >> 5;
+    const long long nw = (static_cast<long long>(gridDim.x) * TPB) >> 5;
+    const uint32_t kpat = static_cast<uint32_t>(K) * 0x01010101u;
+    for (long long ch = wid; ch < nchunk; ch += nw) {  // the same for every lane of the warp
+        const long long p0 = ch * 512 + 16LL * lane;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (vec && ch * 512 + 512 <= P) {
+            const uint4 v = __ldcs(reinterpret_cast<const uint4*>(labels + p0));
+            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+        } else {
+            for (int i = 0; i < 16; ++i)
+                if (p0 + i < P) w[i >> 2] |= static_cast<uint32_t>(labels[p0 + i]) << (8 * (i & 3));
+        }
+        if (!__any_sync(0xFFFFFFFFu, (w[0] | w[1] | w[2] | w[3]) != 0u)) continue;
+        uint32_t over = 0u;
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) over |= __vcmpgtu4(w[q], kpat);
+        if (__any_sync(0xFFFFFFFFu, over != 0u) && lane == 0) atomicCAS(&dm->status, 0, CVA_ERR_LABEL_RANGE);
+        #pragma unroll 1
+        for (int c = 0; c < K; ++c) {
+            const uint32_t pat = static_cast<uint32_t>(c + 1) * 0x01010101u;
+            uint32_t m = 0u;
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) m |= byte_bits(__vcmpeq4(w[q], pat)) << (4 * q);
+            const uint32_t cnt = __popc(m);
+            if (!__any_sync(0xFFFFFFFFu, cnt != 0u)) continue;
+            uint32_t inc = cnt;
+            #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if (lane >= o) inc += u;
+            }
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+            uint32_t base = 0u;
+            if (lane == 0) base = atomicAdd(&dm->cls_count[c], total);
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            unsigned long long pos = static_cast<unsigned long long>(base) + (inc - cnt);
+            for (; m; m &= m - 1, ++pos)
+                if (pos < static_cast<unsigned long long>(cap))
+                    list[static_cast<long long>(c) * cap + static_cast<long long>(pos)] =
+                        static_cast<unsigned int>(p0 + __ffs(m) - 1);
+        }
+    }
+}
+
+// One thread per training row: rows are class-major (class c from the sum
+// of the counts of the classes before it), each taken from its class's
+// region of the list.
 __global__ void __launch_bounds__(TPB)
 k_gather(const uint16_t* __restrict__ cube, int B, long long P, int K, const unsigned int* __restrict__ list,
-         uint16_t* __restrict__ xtr, const DevModel* __restrict__ dm)
+         long long cap, uint16_t* __restrict__ xtr, DevModel* __restrict__ dm)
 {
+    __shared__ unsigned int start[MAXK + 1];
+    __shared__ unsigned long long total;
     if (dm->status != 0) return;
-    unsigned int N = 0;
-    for (int c = 0; c < K; ++c) N += dm->cls_count[c];
+    if (threadIdx.x == 0) {
+        unsigned long long n = 0;
+        start[0] = 0u;
+        #pragma unroll 1
+        for (int c = 0; c < K; ++c) {
+            n += dm->cls_count[c];
+            start[c + 1] = static_cast<unsigned int>(n < 0xFFFFFFFFull ? n : 0xFFFFFFFFull);
+        }
+        total = n;
+    }
+    __syncthreads();
+    const unsigned long long N = total;
+    if (N > static_cast<unsigned long long>(cap)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&dm->status, 0, CVA_ERR_CAPACITY);
+        return;
+    }
     const unsigned int stride = gridDim.x * TPB;
-    for (unsigned int i = blockIdx.x * TPB + threadIdx.x; i < N; i += stride) gather_row(cube, B, P, list, xtr, i);
+    for (unsigned int i = blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
+        int c = 0;
+        while (i >= start[c + 1]) ++c;
+        gather_row(cube, B, P, list[static_cast<long long>(c) * cap + (i - start[c])], xtr, i);
+    }
 }
 
 // ldmatrix / mma.sync wrappers (bf16 inputs, f32 accumulators)
@@ -655,8 +736,7 @@ kb_gather(const PageDev* __restrict__ pages, int n, const BatchTotals* __restric
         const int p = find_page(pages, n, r, [](const PageDev& q) { return q.row0; });
         const PageDev& pg = pages[p];
         if (pg.dm->status != 0) continue;
-        gather_row(pg.cube, pg.B, pg.P, list_pool + pg.row0, xtr_pool + pg.xoff,
-                   static_cast<unsigned int>(r - pg.row0));
+        gather_row(pg.cube, pg.B, pg.P, list_pool[r], xtr_pool + pg.xoff, static_cast<unsigned int>(r - pg.row0));
     }
 }
 
@@ -1113,19 +1193,17 @@ __global__ void k_pca_reset(DevModel* __restrict__ dm, int B)
 }  // namespace
 
 cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const uint8_t* labels, int K,
-                               DevModel* dm, uint16_t* xtr, unsigned int* tiles, unsigned int* list, long long cap,
-                               int num_sms, cudaStream_t s)
+                               DevModel* dm, uint16_t* xtr, unsigned int* list, long long cap, int num_sms,
+                               cudaStream_t s)
 {
     const int vec = (reinterpret_cast<uintptr_t>(labels) % 16 == 0) ? 1 : 0;
-    const long long ntiles = (P + TILE - 1) / TILE;
-    k_tile_count<<<static_cast<unsigned>(ntiles), TPB, 0, s>>>(labels, P, K, B, vec, cap, static_cast<int>(ntiles),
-                                                                 tiles, dm);
+    k_fit_reset<<<1, 256, 0, s>>>(dm, B, K);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_tile_compact<<<static_cast<unsigned>(ntiles), TPB, 0, s>>>(labels, P, K, vec, tiles, list, dm);
+    k_label_scan<<<static_cast<unsigned>(num_sms * 8), TPB, 0, s>>>(labels, P, K, vec, cap, list, dm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_gather<<<static_cast<unsigned>(num_sms * 8), TPB, 0, s>>>(cube, B, P, K, list, xtr, dm);
+    k_gather<<<static_cast<unsigned>(num_sms * 8), TPB, 0, s>>>(cube, B, P, K, list, cap, xtr, dm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 

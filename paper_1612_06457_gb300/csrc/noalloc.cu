@@ -6,8 +6,8 @@
 // applications that forbid device allocations after start-up, and
 // latency-critical loops that must never enter the driver's allocator.  For
 // them cva_fit_project_u8_noalloc keeps every piece of scratch memory the fit
-// needs (the model block, the per-tile workspace, the training list and the
-// gathered training matrix) in one file-scope device array, sized for the
+// needs (the model block, the training list and the gathered training
+// matrix) in one file-scope device array, sized for the
 // limits below, which every GPU that loads this library holds until the
 // process exits.  The caller passes only inputs and outputs.
 //
@@ -27,14 +27,10 @@ using cva::device_visible;
 
 constexpr long long NOALLOC_MAX_PIXELS = 1LL << 26;  // H W
 constexpr long long NOALLOC_MAX_TRAIN = 1LL << 18;   // training pixels
-constexpr long long NOALLOC_MAX_TILES = NOALLOC_MAX_PIXELS / cva::LABEL_TILE;
-
 constexpr size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 constexpr size_t OFF_MODEL = 0;
-constexpr size_t OFF_TILES = align256(OFF_MODEL + sizeof(DevModel));
-constexpr size_t OFF_LIST =
-    align256(OFF_TILES + sizeof(unsigned int) * NOALLOC_MAX_TILES * (cva::MAXK + 1));
-constexpr size_t OFF_XTR = align256(OFF_LIST + sizeof(unsigned int) * NOALLOC_MAX_TRAIN);
+constexpr size_t OFF_LIST = align256(OFF_MODEL + sizeof(DevModel));
+constexpr size_t OFF_XTR = align256(OFF_LIST + sizeof(unsigned int) * NOALLOC_MAX_TRAIN * cva::MAXK);
 constexpr size_t SCRATCH_BYTES =
     align256(OFF_XTR + sizeof(uint16_t) * NOALLOC_MAX_TRAIN * ((cva::MAXB + 1 + 7) & ~7));
 
@@ -42,7 +38,7 @@ static_assert(NOALLOC_MAX_PIXELS <= cva::MAX_PIXELS, "pixel limit above the ABI 
 
 }  // namespace
 
-// The scratch array (about 22 MB in device data, zero at module load).
+// The scratch array (about 38 MB in device data, zero at module load).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
 namespace {
@@ -92,17 +88,15 @@ extern "C" int cva_fit_project_u8_noalloc(const uint16_t* cube, int B, int H, in
     const int rc = scratch_for_current_device(&base, &sms);
     if (rc != CVA_OK) return rc;
     DevModel* dm = reinterpret_cast<DevModel*>(base + OFF_MODEL);
-    unsigned int* tiles = reinterpret_cast<unsigned int*>(base + OFF_TILES);
     unsigned int* list = reinterpret_cast<unsigned int*>(base + OFF_LIST);
     uint16_t* xtr = reinterpret_cast<uint16_t*>(base + OFF_XTR);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    // The label pass's completion ticket is the one word that must start at
-    // zero (the pass resets it itself, the clear covers a call that was cut
-    // short); every other byte is written before it is read within a call, so
-    // the previous call's contents do not leak into this one.
-    cudaError_t e = cudaMemsetAsync(&dm->tile_ticket, 0, sizeof(dm->tile_ticket), s);
-    if (e == cudaSuccess) e = cva::launch_fit_moments(cube, B, P, labels, K, dm, xtr, tiles, list, NOALLOC_MAX_TRAIN, sms, s);
+    // Every word that must start at zero (class counters, moments, status) is
+    // cleared by the fit's first kernel, and every other byte is written
+    // before it is read within a call, so the previous call's contents do not
+    // leak into this one.
+    cudaError_t e = cva::launch_fit_moments(cube, B, P, labels, K, dm, xtr, list, NOALLOC_MAX_TRAIN, sms, s);
     if (e == cudaSuccess) e = cva::launch_fit_finalize(dm, B, K, k, s);
     if (e == cudaSuccess) e = cva::launch_train_range(B, K, xtr, dm, k, sms, s);
     if (e == cudaSuccess) e = cva::launch_project(cube, B, P, dm, k, nullptr, out, dm->train_range, nullptr, sms, s);
