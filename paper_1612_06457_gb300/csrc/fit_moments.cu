@@ -384,64 +384,95 @@ __global__ void k_fit_reset(DevModel* __restrict__ dm, int B, int K)
     }
 }
 
+// One warp's 16-byte share (lane `lane`) of the 512-label chunk `ch`; zero
+// past the page's end.
+__device__ __forceinline__ uint4 chunk_load(const uint8_t* __restrict__ labels, long long P, int vec, long long ch,
+                                            int lane)
+{
+    const long long p0 = ch * 512 + 16LL * lane;
+    if (vec && ch * 512 + 512 <= P) return __ldcs(reinterpret_cast<const uint4*>(labels + p0));
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    for (int i = 0; i < 16; ++i)
+        if (p0 + i < P) w[i >> 2] |= static_cast<uint32_t>(labels[p0 + i]) << (8 * (i & 3));
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // One pass over the labels: the index of every training pixel goes to its
 // class's region of the list (class c at list + c cap, in no particular
-// order).  Each warp takes 512 labels at a time (16 a lane, one 16-byte
-// load) and skips them when none is set; for each class present in them a
-// warp prefix sum of the lanes' counts and one atomic on the class counter
-// give every lane its rows.  The moments are exact integer sums and the
-// ranges minima and maxima, so nothing downstream depends on the order.
-// A label above K sets CVA_ERR_LABEL_RANGE; entries beyond cap are dropped
-// (the gather then reports CVA_ERR_CAPACITY).
+// order).  Each warp takes 512 labels at a time (16 a lane, one 16-byte load,
+// the next chunk's load in flight) and skips them when none is set.  The
+// training pixels are a small part of a page, and per-lane loops over them
+// leave most lanes idle, so everything runs converged on the warp:
+//   * one ballot per byte position compacts the chunk's labelled pixels into
+//     the warp's staging area in shared memory (pixel offset | label << 16);
+//   * 32 entries at a time, one ballot per class counts them, lane c adds the
+//     chunk's count of class c to that class's counter (all classes' atomics
+//     in flight together), and the same ballots again give every entry its
+//     row: the class's base plus its rank among the lanes below it.
+// The moments are exact integer sums and the ranges minima and maxima, so
+// nothing downstream depends on the order.  A label above K sets
+// CVA_ERR_LABEL_RANGE and is not listed; entries beyond cap are dropped (the
+// gather then reports CVA_ERR_CAPACITY).
 __global__ void __launch_bounds__(TPB)
 k_label_scan(const uint8_t* __restrict__ labels, long long P, int K, int vec, long long cap,
              unsigned int* __restrict__ list, DevModel* __restrict__ dm)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ uint32_t stage[NW][512];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t below = (1u << lane) - 1u;
     const long long nchunk = (P + 511) / 512;
     const long long wid = (static_cast<long long>(blockIdx.x) * TPB + threadIdx.x) >> 5;
     const long long nw = (static_cast<long long>(gridDim.x) * TPB) >> 5;
-    const uint32_t kpat = static_cast<uint32_t>(K) * 0x01010101u;
-    for (long long ch = wid; ch < nchunk; ch += nw) {  // the same for every lane of the warp
-        const long long p0 = ch * 512 + 16LL * lane;
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
-        if (vec && ch * 512 + 512 <= P) {
-            const uint4 v = __ldcs(reinterpret_cast<const uint4*>(labels + p0));
-            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
-        } else {
-            for (int i = 0; i < 16; ++i)
-                if (p0 + i < P) w[i >> 2] |= static_cast<uint32_t>(labels[p0 + i]) << (8 * (i & 3));
-        }
-        if (!__any_sync(0xFFFFFFFFu, (w[0] | w[1] | w[2] | w[3]) != 0u)) continue;
-        uint32_t over = 0u;
+    uint32_t* st = stage[warp];
+    bool bad = false;
+    long long ch = wid;
+    uint4 next = make_uint4(0u, 0u, 0u, 0u);
+    if (ch < nchunk) next = chunk_load(labels, P, vec, ch, lane);
+    for (; ch < nchunk; ch += nw) {  // the same for every lane of the warp
+        const uint4 x = next;
+        if (ch + nw < nchunk) next = chunk_load(labels, P, vec, ch + nw, lane);
+        if (!__any_sync(0xFFFFFFFFu, (x.x | x.y | x.z | x.w) != 0u)) continue;
+        const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+        int T = 0;  // entries staged, in (byte position, lane) order
         #pragma unroll
-        for (int q = 0; q < 4; ++q) over |= __vcmpgtu4(w[q], kpat);
-        if (__any_sync(0xFFFFFFFFu, over != 0u) && lane == 0) atomicCAS(&dm->status, 0, CVA_ERR_LABEL_RANGE);
-        #pragma unroll 1
-        for (int c = 0; c < K; ++c) {
-            const uint32_t pat = static_cast<uint32_t>(c + 1) * 0x01010101u;
-            uint32_t m = 0u;
-            #pragma unroll
-            for (int q = 0; q < 4; ++q) m |= byte_bits(__vcmpeq4(w[q], pat)) << (4 * q);
-            const uint32_t cnt = __popc(m);
-            if (!__any_sync(0xFFFFFFFFu, cnt != 0u)) continue;
-            uint32_t inc = cnt;
-            #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-                if (lane >= o) inc += u;
+        for (int j = 0; j < 16; ++j) {
+            const uint32_t v = (w[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v != 0u);
+            if (bal) {
+                if (v) st[T + __popc(bal & below)] = static_cast<uint32_t>(16 * lane + j) | (v << 16);
+                T += __popc(bal);
             }
-            const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
-            uint32_t base = 0u;
-            if (lane == 0) base = atomicAdd(&dm->cls_count[c], total);
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            unsigned long long pos = static_cast<unsigned long long>(base) + (inc - cnt);
-            for (; m; m &= m - 1, ++pos)
-                if (pos < static_cast<unsigned long long>(cap))
-                    list[static_cast<long long>(c) * cap + static_cast<long long>(pos)] =
-                        static_cast<unsigned int>(p0 + __ffs(m) - 1);
         }
+        __syncwarp();
+        unsigned int mine = 0u;  // lane c: the chunk's count of class c
+        for (int i0 = 0; i0 < T; i0 += 32) {
+            const uint32_t v = (i0 + lane < T) ? (st[i0 + lane] >> 16) : 0u;
+            bad |= v > static_cast<uint32_t>(K);
+            for (int c = 0; c < K; ++c) {
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v == static_cast<uint32_t>(c + 1));
+                if (lane == c) mine += __popc(bal);
+            }
+        }
+        unsigned int run = 0u;   // lane c: the next row of class c
+        if (lane < K && mine) run = atomicAdd(&dm->cls_count[lane], mine);
+        for (int i0 = 0; i0 < T; i0 += 32) {
+            const uint32_t e = (i0 + lane < T) ? st[i0 + lane] : 0u;
+            const uint32_t v = e >> 16;
+            for (int c = 0; c < K; ++c) {
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v == static_cast<uint32_t>(c + 1));
+                const unsigned int base = __shfl_sync(0xFFFFFFFFu, run, c);
+                if (v == static_cast<uint32_t>(c + 1)) {
+                    const unsigned long long pos = static_cast<unsigned long long>(base) + __popc(bal & below);
+                    if (pos < static_cast<unsigned long long>(cap))
+                        list[static_cast<long long>(c) * cap + static_cast<long long>(pos)] =
+                            static_cast<unsigned int>(ch * 512 + (e & 0xFFFFu));
+                }
+                if (lane == c) run += __popc(bal);
+            }
+        }
+        __syncwarp();  // the staging area is rewritten by the next chunk
     }
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicCAS(&dm->status, 0, CVA_ERR_LABEL_RANGE);
 }
 
 // One thread per training row: rows are class-major (class c from the sum
@@ -924,11 +955,6 @@ k_pca_moments(const uint16_t* __restrict__ cube, int B, long long P, const uint8
 // The exact moments of every class as a flat array: class c, then the upper
 // triangle a <= b of the (B+1) x (B+1) augmented moment matrix in row-major
 // order (entry (a, b) at c W + a (B+1) - a (a-1)/2 + (b - a), W = (B+1)(B+2)/2).
-__device__ inline int tri_index(int a, int b, int BA)
-{
-    return a * BA - a * (a - 1) / 2 + (b - a);
-}
-
 __global__ void k_moments_export(const DevModel* __restrict__ dm, int B, int K, long long* __restrict__ out)
 {
     const int BA = B + 1, per = BA * (BA + 1) / 2;
