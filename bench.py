@@ -39,8 +39,8 @@ L2_BYTES = 126 * 1024 * 1024
 # DRAM traffic of one k_project_v8<3, u8> launch on the 23-band 4096 x 4096
 # cube, from ncu (dram__bytes_read.sum + dram__bytes_write.sum), valid while
 # the projection source hashes to PROJECT_SRC_SHA256; null otherwise.
-PROJECT_TRAFFIC_BYTES = 771842304 + 34762240
-PROJECT_SRC_SHA256 = "57d0496388e7138ec94d32da9522593e4b14511f223ad823e7e2b508670a1f47"
+PROJECT_TRAFFIC_BYTES = 771890688 + 44134144
+PROJECT_SRC_SHA256 = "83543891041dfd7f3435d85e1e8347e7975a7d7e962662ee7ed28749e054b195"
 
 
 def _args():
