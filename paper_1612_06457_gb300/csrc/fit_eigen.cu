@@ -181,17 +181,6 @@ __device__ inline void team_sync()
     else __syncthreads();
 }
 
-// Maximum over the team: warp 0 (TEAM = 32) by shuffles, or the whole block.
-template <int NM, int TEAM>
-__device__ inline float team_maxf(SymEig<NM>& e, float v, int slot)
-{
-    if (TEAM == 32) {
-        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-        return v;
-    }
-    return block_maxf(e, v, slot);
-}
-
 // Cyclic Jacobi on e.Tf (round-robin order) in FP32, accumulating the
 // rotations in e.Wf.  Run by warp 0 alone (TEAM = 32) for orders 5 to 8 or by
 // the whole block (TEAM = TPB) above, which applies the rotations of a round
@@ -283,7 +272,7 @@ __device__ void jacobi_team(SymEig<NM>& e, int n)
 // matrix and the accumulated rotations in registers and the rotations taken
 // in row-cyclic order: at these orders a warp spends most of each round on
 // shared-memory round trips and warp barriers, which a single thread avoids.
-// Orders up to 4 keep the kernel under 64 registers (two CTAs an SM for the
+// Orders up to 4 keep the kernel at 56 registers (two CTAs an SM for the
 // batched form, as its shared memory allows); orders 5 to 8 in registers
 // took 156.
 template <int N, int NM>
@@ -360,8 +349,7 @@ __device__ void jacobi_serial(SymEig<NM>& e)
 // refined in double-float by the Ogita-Aishima iteration for symmetric
 // eigendecompositions (T. Ogita, K. Aishima, "Iterative refinement for
 // symmetric eigenvalue decomposition", Japan J. Indust. Appl. Math. 35, 2018),
-// on warp 0 alone up to order 8 (warp barriers only) and with its matrix
-// products spread over the whole block above.  Leaves the eigenvectors in e.W
+// whose matrix products are spread over the whole block.  Leaves the eigenvectors in e.W
 // (columns) and the eigenvalues in e.lam, unsorted.  Every thread of the
 // block calls it.
 //
@@ -430,18 +418,30 @@ __device__ bool cluster_rotations(SymEig<NM>& e, int n, float delta, float lm)
     return rot;
 }
 
-// Ogita-Aishima refinement of the eigenvectors of e.T from the FP32 start in
-// e.Wf, by warp 0 alone (TEAM = 32: orders up to 8, at most 64 entries, two
-// an item per lane and warp barriers only) or by the whole block above.
-template <int NM, int TEAM>
-__device__ void refine_team(SymEig<NM>& e, int n, bool canonical)
+template <int NM>
+__device__ void sym_eig(SymEig<NM>& e, int n, bool canonical)
 {
-    const int me = TEAM == 32 ? static_cast<int>(threadIdx.x & 31) : static_cast<int>(threadIdx.x);
+    const int tid = threadIdx.x;
+    if (n > 8) {
+        jacobi_team<NM, TPB>(e, n);
+    } else if (n > 4) {
+        if ((tid >> 5) == 0) jacobi_team<NM, 32>(e, n);
+    } else if (tid == 0) {
+        switch (n) {
+            case 1: jacobi_serial<1>(e); break;
+            case 2: jacobi_serial<2>(e); break;
+            case 3: jacobi_serial<3>(e); break;
+            default: jacobi_serial<4>(e); break;
+        }
+    }
+    __syncthreads();
+
+    // Ogita-Aishima refinement of the eigenvectors W of T in double-float
     const int nn = n * n;
-    for (int q = me; q < nn; q += TEAM) e.W[q / n][q % n] = df_from(e.Wf[q / n][q % n]);
-    team_sync<TEAM>();
+    for (int q = tid; q < nn; q += TPB) e.W[q / n][q % n] = df_from(e.Wf[q / n][q % n]);
+    __syncthreads();
     for (int it = 0; it < REFINE_STEPS; ++it) {
-        for (int q = me; q < nn; q += TEAM) {
+        for (int q = tid; q < nn; q += TPB) {
             const int a = q / n, b = q % n;
             df r = df_from(0.0f), tw = df_from(0.0f);
             #pragma unroll 1
@@ -452,9 +452,9 @@ __device__ void refine_team(SymEig<NM>& e, int n, bool canonical)
             e.R[a][b] = df_sub(df_from(a == b ? 1.0f : 0.0f), r);  // I - W^T W
             e.TW[a][b] = tw;
         }
-        team_sync<TEAM>();
+        __syncthreads();
         float so = 0.0f, lm = 0.0f, rm = 0.0f;
-        for (int q = me; q < nn; q += TEAM) {
+        for (int q = tid; q < nn; q += TPB) {
             const int a = q / n, b = q % n;
             df sv = df_from(0.0f);
             #pragma unroll 1
@@ -464,24 +464,24 @@ __device__ void refine_team(SymEig<NM>& e, int n, bool canonical)
             else lm = fmaxf(lm, fabsf(sv.hi));
             rm = fmaxf(rm, fabsf(e.R[a][b].hi));
         }
-        so = team_maxf<NM, TEAM>(e, so, 0);
-        lm = team_maxf<NM, TEAM>(e, lm, 1);
-        rm = team_maxf<NM, TEAM>(e, rm, 2);
+        so = block_maxf(e, so, 0);
+        lm = block_maxf(e, lm, 1);
+        rm = block_maxf(e, rm, 2);
         const float delta = 2.0f * (so + lm * rm);  // cluster threshold
-        if (me < n) {  // lambda_i = s_ii / (1 - r_ii) = s_ii (1 + r_ii + r_ii^2 + ...)
-            const df r = e.R[me][me];
-            e.lam[me] = df_mul(e.S[me][me], df_add(df_from(1.0f), df_mul(r, df_add(df_from(1.0f), r))));
+        if (tid < n) {  // lambda_i = s_ii / (1 - r_ii) = s_ii (1 + r_ii + r_ii^2 + ...)
+            const df r = e.R[tid][tid];
+            e.lam[tid] = df_mul(e.S[tid][tid], df_add(df_from(1.0f), df_mul(r, df_add(df_from(1.0f), r))));
         }
-        team_sync<TEAM>();
-        if (me == 0) {
+        __syncthreads();
+        if (tid == 0) {
             e.rotated = cluster_rotations(e, n, delta, lm) ? 1 : 0;
             if (e.rotated) e.last_correction = 1.0f;  // not converged if the steps end here
         }
-        team_sync<TEAM>();
+        __syncthreads();
         if (e.rotated) continue;  // the step starts over from the rotated W
         float emax = 0.0f;
         const float lnull = 1e-12f * lm;  // eigenvalue-0 columns (the rank test of the caller)
-        for (int q = me; q < nn; q += TEAM) {
+        for (int q = tid; q < nn; q += TPB) {
             const int a = q / n, b = q % n;
             df ev;
             const df gap = df_sub(e.lam[b], e.lam[a]);
@@ -498,49 +498,21 @@ __device__ void refine_team(SymEig<NM>& e, int n, bool canonical)
             if (canonical) w = (lb > lnull) ? sqrtf(fmaxf(la, 0.0f) / lb) : 0.0f;
             emax = fmaxf(emax, fabsf(ev.hi) * w);
         }
-        team_sync<TEAM>();  // E complete; the red rows are free again
-        emax = team_maxf<NM, TEAM>(e, emax, 0);
-        for (int q = me; q < nn; q += TEAM) {
+        __syncthreads();  // E complete; the red rows are free again
+        emax = block_maxf(e, emax, 0);
+        for (int q = tid; q < nn; q += TPB) {
             const int a = q / n, b = q % n;
             df d = df_from(0.0f);
             #pragma unroll 1
             for (int k = 0; k < n; ++k) d = df_fma(d, e.W[a][k], e.E[k][b]);  // W E
             e.TW[a][b] = d;
         }
-        team_sync<TEAM>();
-        for (int q = me; q < nn; q += TEAM) e.W[q / n][q % n] = df_add(e.W[q / n][q % n], e.TW[q / n][q % n]);
-        team_sync<TEAM>();
-        if (me == 0) e.last_correction = emax;
+        __syncthreads();
+        for (int q = tid; q < nn; q += TPB) e.W[q / n][q % n] = df_add(e.W[q / n][q % n], e.TW[q / n][q % n]);
+        __syncthreads();
+        if (tid == 0) e.last_correction = emax;
         if (emax < REFINE_DONE) break;  // the next correction would be of order 1e-12
     }
-}
-
-
-template <int NM>
-__device__ void sym_eig(SymEig<NM>& e, int n, bool canonical)
-{
-    const int tid = threadIdx.x;
-    if (n > 8) {
-        jacobi_team<NM, TPB>(e, n);
-        __syncthreads();
-        refine_team<NM, TPB>(e, n, canonical);
-    } else if ((tid >> 5) == 0) {
-        if (n > 4) {
-            jacobi_team<NM, 32>(e, n);
-        } else {
-            if (tid == 0) {
-                switch (n) {
-                    case 1: jacobi_serial<1>(e); break;
-                    case 2: jacobi_serial<2>(e); break;
-                    case 3: jacobi_serial<3>(e); break;
-                    default: jacobi_serial<4>(e); break;
-                }
-            }
-            __syncwarp();
-        }
-        refine_team<NM, 32>(e, n, canonical);
-    }
-    __syncthreads();
 }
 
 // Complete U[:, j0 .. j1) to an orthonormal set with pivoted Gram-Schmidt:

@@ -311,6 +311,24 @@ def test_max_bands_and_classes():
     m.close()
 
 
+def test_every_pixel_labelled_in_sixteen_classes():
+    """Every pixel is a training pixel, labelled with its class out of 16:
+    the label pass then places up to 512 pixels of a chunk in all 16
+    classes at once (16 rounds of 32 entries).  Counts exact, fit against
+    the oracle."""
+    _skip_without_gpu()
+    import dataclasses
+
+    w = make_workload(118, 20, 263, 301, 16, tuple([200] * 16), 15, separation=(1.0, 4.0))
+    lab = (w.classmap + 1).astype(np.uint8)
+    w = dataclasses.replace(w, labels=lab, n_train=tuple(int((lab == c + 1).sum()) for c in range(16)))
+    ref = oracle.fit(w.cube, w.labels, w.K)
+    m, cube, labels, g = _gpu_fit(w)
+    assert g["n"].tolist() == list(w.n_train) and sum(w.n_train) == w.H * w.W
+    _check_fit(g, ref, w.K, w.B, w.B)
+    m.close()
+
+
 def test_full_size_23_band_4096x4096_cube():
     """The 23-band 4096 x 4096 cube, 4 classes of 50 000 training pixels,
     3 variates, exactly as the benchmark runs it (fit, then fused projection
