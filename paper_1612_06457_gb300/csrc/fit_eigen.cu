@@ -24,7 +24,7 @@
 //     square root, the critical path of the elimination);
 //  3. L^-1 Sb L^-T = G G^T has rank <= K - 1 and the same non-zero
 //     eigenvalues as the K x K matrix T = G^T G.  T is diagonalized by the
-//     cyclic Jacobi method in FP32 (one thread, in registers, up to order 4;
+//     cyclic Jacobi method in FP32 (one thread, in registers, up to order 8;
 //     round-robin order on one warp up to order 8 and over the block above),
 //     and the eigenvectors are then
 //     refined in double-float by the Ogita-Aishima iteration (usually one or
@@ -184,7 +184,7 @@ __device__ inline void team_sync()
 // Cyclic Jacobi on e.Tf (round-robin order) in FP32, accumulating the
 // rotations in e.Wf.  Run by warp 0 alone (TEAM = 32) for orders 5 to 8 or by
 // the whole block (TEAM = TPB) above, which applies the rotations of a round
-// in parallel over all its threads; jacobi_serial takes orders up to 4.
+// in parallel over all its threads; jacobi_serial takes the orders below.
 template <int NM, int TEAM>
 __device__ void jacobi_team(SymEig<NM>& e, int n)
 {
@@ -272,9 +272,11 @@ __device__ void jacobi_team(SymEig<NM>& e, int n)
 // matrix and the accumulated rotations in registers and the rotations taken
 // in row-cyclic order: at these orders a warp spends most of each round on
 // shared-memory round trips and warp barriers, which a single thread avoids.
-// Orders up to 4 keep the kernel at 56 registers (two CTAs an SM for the
-// batched form, as its shared memory allows); orders 5 to 8 in registers
-// took 156.
+// The fit kernels (one page, and one CTA a page in the batched form) take it
+// up to order 8.  They then need 155 registers, one CTA an SM (a batch of
+// more pages than SMs runs its eigensolves in two waves); capped at order 4
+// they needed 56 and took longer (ncu on the 4-class benchmark fit: 46-48 us
+// against 42 us; the order-5 Jacobi on warp 0 was slower still).
 template <int N, int NM>
 __device__ void jacobi_serial(SymEig<NM>& e)
 {
@@ -344,7 +346,7 @@ __device__ void jacobi_serial(SymEig<NM>& e)
 
 // Eigen-decomposition of the symmetric n x n matrix e.T (n <= NM, scaled to
 // about unit norm; e.Tf holds its FP32 copy and e.Wf the identity on entry).
-// The cyclic Jacobi method in FP32 runs on thread 0 for orders up to 4, on
+// The cyclic Jacobi method in FP32 runs on thread 0 for orders up to SER, on
 // warp 0 up to 8 and on the whole block above; the eigenvectors are then
 // refined in double-float by the Ogita-Aishima iteration for symmetric
 // eigendecompositions (T. Ogita, K. Aishima, "Iterative refinement for
@@ -418,20 +420,30 @@ __device__ bool cluster_rotations(SymEig<NM>& e, int n, float delta, float lm)
     return rot;
 }
 
-template <int NM>
+template <int NM, int SER>
 __device__ void sym_eig(SymEig<NM>& e, int n, bool canonical)
 {
     const int tid = threadIdx.x;
     if (n > 8) {
         jacobi_team<NM, TPB>(e, n);
-    } else if (n > 4) {
+    } else if (n > SER) {
         if ((tid >> 5) == 0) jacobi_team<NM, 32>(e, n);
     } else if (tid == 0) {
         switch (n) {
             case 1: jacobi_serial<1>(e); break;
             case 2: jacobi_serial<2>(e); break;
             case 3: jacobi_serial<3>(e); break;
-            default: jacobi_serial<4>(e); break;
+            case 4: jacobi_serial<4>(e); break;
+            default:
+                if constexpr (SER >= 8) {
+                    switch (n) {
+                        case 5: jacobi_serial<5>(e); break;
+                        case 6: jacobi_serial<6>(e); break;
+                        case 7: jacobi_serial<7>(e); break;
+                        default: jacobi_serial<8>(e); break;
+                    }
+                }
+                break;
         }
     }
     __syncthreads();
@@ -570,6 +582,7 @@ __device__ void complete_basis(FinSmem& sm, int B, int j0, int j1)
     }
 }
 
+template <int SER>
 __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restrict__ dm, int B, int K, int nvec)
 {
     const MomShape sh = mom_shape(B);
@@ -796,7 +809,7 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
         }
         __syncthreads();
     } else {
-        sym_eig<MAXK>(sm.eig, n, true);
+        sym_eig<MAXK, SER>(sm.eig, n, true);
         __syncthreads();
     }
     if (!(sm.eig.last_correction < REFINE_DONE)) {
@@ -928,7 +941,7 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
 __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm, int B, int K, int nvec)
 {
     extern __shared__ __align__(16) unsigned char fin_dyn[];
-    fit_finalize_body(*reinterpret_cast<FinSmem*>(fin_dyn), dm, B, K, nvec);
+    fit_finalize_body<8>(*reinterpret_cast<FinSmem*>(fin_dyn), dm, B, K, nvec);
 }
 
 // Batched form: one CTA per page, all pages at once; the eigenvalues are
@@ -937,7 +950,7 @@ __global__ void __launch_bounds__(TPB) kb_fit_finalize(const PageDev* __restrict
 {
     extern __shared__ __align__(16) unsigned char fin_dyn[];
     const PageDev& pg = pages[blockIdx.x];
-    fit_finalize_body(*reinterpret_cast<FinSmem*>(fin_dyn), pg.dm, pg.B, pg.K, pg.k);
+    fit_finalize_body<8>(*reinterpret_cast<FinSmem*>(fin_dyn), pg.dm, pg.B, pg.K, pg.k);
     __syncthreads();
     if (pg.eigvals && threadIdx.x < pg.B && pg.dm->status == 0) pg.eigvals[threadIdx.x] = pg.dm->lam[threadIdx.x];
 }
@@ -1013,7 +1026,7 @@ __global__ void __launch_bounds__(TPB) k_pca_finalize(DevModel* __restrict__ dm,
         sm.eig.Wf[a][b] = (a == b) ? 1.0f : 0.0f;
     }
     __syncthreads();
-    sym_eig<MAXB>(sm.eig, B, false);
+    sym_eig<MAXB, 4>(sm.eig, B, false);
     __syncthreads();
     if (!(sm.eig.last_correction < REFINE_DONE)) {
         if (tid == 0) set_status(dm, CVA_ERR_NO_CONVERGENCE);

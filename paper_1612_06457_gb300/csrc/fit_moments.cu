@@ -9,23 +9,14 @@
 // depend on the order of accumulation, so the result is deterministic even
 // though thread blocks merge their partial sums with atomics.
 //
-// Four kernels for one page; the label map is cut into tiles of 16384
-// labels, one CTA per tile in the label passes (each thread holds 64 labels
-// from four 128-bit loads in flight, compared four bytes at a time; tiles of
-// 32768 labels, one wave of CTAs, measured 19.4 + 29.5 us against 17.9 +
-// 22.9 us for the two passes):
-//   k_tile_count    training pixels of each class in the tile, and whether
-//                   the tile holds a label above K; the last CTA to finish
-//                   (atomic ticket, no waiting) then takes the prefix sums of
-//                   the tile counts (one warp per class), giving each tile
-//                   its first row within every class segment of the
-//                   class-major training list, and writes the class totals,
-//                   the fit's status word and the reset of the moment
-//                   accumulators;
-//   k_tile_compact  re-reads the tile and writes the pixel index of every
-//                   training pixel to its row of the class-major list
-//                   (block-wide scan of packed per-thread class counts, then
-//                   class by class one store per training pixel);
+// Four passes for one page after a one-CTA reset (k_fit_reset):
+//   k_label_scan    one pass over the labels: each warp takes 512 labels at
+//                   a time (one 16-byte load a lane) and, converged, stages
+//                   the labelled ones in shared memory by ballots, counts
+//                   them by class with one ballot per class, reserves their
+//                   rows with one atomic per class (lane c for class c) and
+//                   writes every pixel index to its class's region of the
+//                   list (class c at list + c cap, in no fixed order);
 //   k_gather        one thread per listed pixel, all band loads in flight:
 //                   the augmented row (x_0 .. x_{B-1}, 1, 0 ..) of the
 //                   class-major training matrix (16-byte rows);
@@ -34,8 +25,16 @@
 //                   registers while a CTA stays on one class and are merged
 //                   into the model with 64-bit integer atomics when it moves
 //                   on.  The "1" column yields n_c and s_c in the same pass.
+// Training pixels are a small share of a page, so loops of each lane over its
+// own labels would leave most lanes idle: the label passes stay converged on
+// the warp and their cost is the labels' one read plus a little work per
+// chunk that holds a training pixel.
 // The same passes in batched form (kb_*: the flattened work of many pages,
-// see batch.cu), and the moments of every selected pixel of a page for the
+// see batch.cu), where the training lists are sized exactly: a count pass
+// over tiles of 16384 labels (the same staged chunks; each page's last CTA
+// takes the prefix sums over its tiles) and a compaction pass that reserves
+// each chunk's rows inside its tile's share with shared-memory atomics; and
+// the moments of every selected pixel of a page for the
 // principal components (k_pca_moments, straight from the cube).
 #include "cva_internal.cuh"
 
@@ -69,78 +68,6 @@ __device__ inline void load_tile(const uint8_t* __restrict__ labels, long long t
             for (int i = 0; i < 16; ++i)
                 if (p0 + i < P) w[u][i >> 2] |= static_cast<uint32_t>(labels[p0 + i]) << (8 * (i & 3));
         }
-    }
-}
-
-// Class counters packed four to a 64-bit word (16-bit fields; a tile holds
-// 16384 labels, so no field carries into the next).
-__device__ inline unsigned int field(const unsigned long long (&v)[4], int c)
-{
-    const unsigned long long w = (c < 4) ? v[0] : (c < 8) ? v[1] : (c < 12) ? v[2] : v[3];
-    return static_cast<unsigned int>((w >> (16 * (c & 3))) & 0xFFFFull);
-}
-
-// Block-wide exclusive scan of packed counters (`nwords` words used).
-// `wsum` is NW x 4 words of shared memory; the caller syncs before reusing it.
-__device__ inline void block_scan_packed(const unsigned long long (&cnt)[4], int nwords,
-                                         unsigned long long (*wsum)[4], unsigned long long (&excl)[4],
-                                         unsigned long long (&total)[4])
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long inc[4];
-    #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        inc[q] = cnt[q];
-        if (q < nwords) {
-            #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, inc[q], o);
-                if (lane >= o) inc[q] += v;
-            }
-        }
-    }
-    if (lane == 31) {
-        #pragma unroll
-        for (int q = 0; q < 4; ++q) wsum[warp][q] = inc[q];
-    }
-    __syncthreads();
-    #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        unsigned long long before = 0ull, all = 0ull;
-        if (q < nwords) {
-            #pragma unroll
-            for (int w2 = 0; w2 < NW; ++w2) {
-                const unsigned long long v = wsum[w2][q];
-                before += (w2 < warp) ? v : 0ull;
-                all += v;
-            }
-        }
-        excl[q] = before + inc[q] - cnt[q];
-        total[q] = all;
-    }
-}
-
-// Four bits, one per byte of `r` (each byte 0x00 or 0xFF): bit i from byte i.
-__device__ inline uint32_t byte_bits(uint32_t r)
-{
-    const uint32_t t = r & 0x01010101u;
-    return (t | (t >> 7) | (t >> 14) | (t >> 21)) & 0xFu;
-}
-
-// Per-class counts of 16 labels (4 words) added into 16-bit fields, four
-// classes per 64-bit word; byte compares four at a time.
-__device__ inline void count16(const uint32_t (&w)[4], int K, unsigned long long (&cnt)[4])
-{
-    // a rolled loop keeps the label passes' code small (they run it four
-    // times per thread, and instruction fetch limited them when unrolled)
-    #pragma unroll 1
-    for (int c = 0; c < K; ++c) {
-        const uint32_t pat = static_cast<uint32_t>(c + 1) * 0x01010101u;
-        uint32_t n = 0;
-        #pragma unroll
-        for (int q = 0; q < 4; ++q) n += __popc(__vcmpeq4(w[q], pat) & 0x01010101u);
-        const unsigned long long add = static_cast<unsigned long long>(n) << (16 * (c & 3));
-        if (c < 4) cnt[0] += add; else if (c < 8) cnt[1] += add; else if (c < 12) cnt[2] += add; else cnt[3] += add;
     }
 }
 
@@ -215,53 +142,95 @@ __device__ void scan_tiles(int ntiles, int K, int B, long long cap, unsigned int
     }
 }
 
+// The labelled pixels of one warp's 512 labels (16 a lane, in w) staged in
+// `st` in (byte position, lane) order, one ballot per byte position; an
+// entry is the pixel's offset in the 512 | its label << 16.  Returns how many.
+// Every lane of the warp calls it; st is read after it returns.
+__device__ __forceinline__ int stage_chunk(const uint32_t (&w)[4], uint32_t* st, int lane)
+{
+    const uint32_t below = (1u << lane) - 1u;
+    int T = 0;
+    #pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const uint32_t v = (w[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v != 0u);
+        if (bal) {
+            if (v) st[T + __popc(bal & below)] = static_cast<uint32_t>(16 * lane + j) | (v << 16);
+            T += __popc(bal);
+        }
+    }
+    __syncwarp();
+    return T;
+}
+
+// Class counts of T staged entries, one ballot per class and 32 entries:
+// added to `mine` on lane c for class c.  Sets `over` for a label above K.
+__device__ __forceinline__ void count_staged(const uint32_t* st, int T, int K, int lane, unsigned int& mine, bool& over)
+{
+    for (int i0 = 0; i0 < T; i0 += 32) {
+        const uint32_t v = (i0 + lane < T) ? (st[i0 + lane] >> 16) : 0u;
+        over |= v > static_cast<uint32_t>(K);
+        for (int c = 0; c < K; ++c) {
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v == static_cast<uint32_t>(c + 1));
+            if (lane == c) mine += __popc(bal);
+        }
+    }
+}
+
+// Rows for T staged entries: class c's next row is lane c's `run` (advanced
+// past them); each entry goes to list[c * stride + row] as p0 + its offset.
+__device__ __forceinline__ void place_staged(const uint32_t* st, int T, int K, int lane, unsigned int run,
+                                             unsigned long long p0, unsigned int* __restrict__ list,
+                                             long long stride, long long cap)
+{
+    const uint32_t below = (1u << lane) - 1u;
+    for (int i0 = 0; i0 < T; i0 += 32) {
+        const uint32_t e = (i0 + lane < T) ? st[i0 + lane] : 0u;
+        const uint32_t v = e >> 16;
+        for (int c = 0; c < K; ++c) {
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v == static_cast<uint32_t>(c + 1));
+            const unsigned int base = __shfl_sync(0xFFFFFFFFu, run, c);
+            if (v == static_cast<uint32_t>(c + 1)) {
+                const unsigned long long pos = static_cast<unsigned long long>(base) + __popc(bal & below);
+                if (pos < static_cast<unsigned long long>(cap))
+                    list[static_cast<long long>(c) * stride + static_cast<long long>(pos)] =
+                        static_cast<unsigned int>(p0 + (e & 0xFFFFu));
+            }
+            if (lane == c) run += __popc(bal);
+        }
+    }
+}
+
 // One tile's class counts (tile `tile` of the page); the page's last CTA to
 // finish takes the prefix sums.
 __device__ __forceinline__ void tile_count_body(const uint8_t* __restrict__ labels, long long P, int K, int B, int vec,
                                                 long long cap, int ntiles, unsigned int* __restrict__ tiles,
                                                 DevModel* __restrict__ dm, int tile)
 {
-    __shared__ unsigned long long wsum[NW][4];
+    __shared__ uint32_t stage[NW][512];
+    __shared__ unsigned int scnt[MAXK];
     __shared__ int bad;
     __shared__ int last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < MAXK) scnt[tid] = 0u;
     if (tid == 0) bad = 0;
     uint32_t w[NG][4];
     load_tile(labels, static_cast<long long>(tile) * TILE, P, vec, w);
-    unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
-    const uint32_t kpat = static_cast<uint32_t>(K) * 0x01010101u;
-    uint32_t over = 0;
+    __syncthreads();
+    // warp w's chunks: labels u SUB + 512 w .. + 511 of the tile, u < NG
+    unsigned int mine = 0u;
+    bool over = false;
     #pragma unroll
     for (int u = 0; u < NG; ++u) {
-        if ((w[u][0] | w[u][1] | w[u][2] | w[u][3]) == 0u) continue;
-        count16(w[u], K, cnt);
-        #pragma unroll
-        for (int q = 0; q < 4; ++q) over |= __vcmpgtu4(w[u][q], kpat);
+        if (!__any_sync(0xFFFFFFFFu, (w[u][0] | w[u][1] | w[u][2] | w[u][3]) != 0u)) continue;
+        const int T = stage_chunk(w[u], stage[warp], lane);
+        count_staged(stage[warp], T, K, lane, mine, over);
+        __syncwarp();  // the stage is rewritten by the next chunk
     }
-    #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        for (int o = 16; o > 0; o >>= 1) cnt[q] += __shfl_xor_sync(0xFFFFFFFFu, cnt[q], o);
-    if (lane == 0) {
-        #pragma unroll
-        for (int q = 0; q < 4; ++q) wsum[warp][q] = cnt[q];
-    }
-    __syncthreads();  // also orders the bad-flag reset before the update below
-    if (over) bad = 1;
+    if (lane < K && mine) atomicAdd(&scnt[lane], mine);
+    if (__any_sync(0xFFFFFFFFu, over) && lane == 0) bad = 1;
     __syncthreads();
-    if (tid <= K) {
-        unsigned int v;
-        if (tid == K) {
-            v = static_cast<unsigned int>(bad);
-        } else {
-            unsigned long long t[4] = {0ull, 0ull, 0ull, 0ull};
-            #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                #pragma unroll
-                for (int w2 = 0; w2 < NW; ++w2) t[q] += wsum[w2][q];
-            v = field(t, tid);
-        }
-        tiles[static_cast<long long>(tile) * (K + 1) + tid] = v;
-    }
+    if (tid <= K) tiles[static_cast<long long>(tile) * (K + 1) + tid] = (tid == K) ? static_cast<unsigned int>(bad) : scnt[tid];
     // the last CTA to finish (atomic ticket after a fence) scans the counts;
     // no CTA ever waits for another
     __threadfence();
@@ -273,15 +242,6 @@ __device__ __forceinline__ void tile_count_body(const uint8_t* __restrict__ labe
     scan_tiles(ntiles, K, B, cap, tiles, dm);
 }
 
-// Adds k to the 16-bit class counter c of packed counters v.
-__device__ inline void bump_by(unsigned long long (&v)[4], int c, unsigned int k)
-{
-    const unsigned long long add = static_cast<unsigned long long>(k) << (16 * (c & 3));
-    if (c < 4) v[0] += add;
-    else if (c < 8) v[1] += add;
-    else if (c < 12) v[2] += add;
-    else v[3] += add;
-}
 
 // One tile's training pixels written to their rows of the class-major list.
 // `cls_count` gives the class segment starts, `tiles` each tile's first row
@@ -291,9 +251,9 @@ __device__ __forceinline__ void tile_compact_body(const uint8_t* __restrict__ la
                                                   const unsigned int* __restrict__ cls_count,
                                                   unsigned int* __restrict__ list, int tile)
 {
-    __shared__ unsigned long long wsum[NW][4];
-    __shared__ unsigned int base[MAXK];
-    const int tid = threadIdx.x;
+    __shared__ uint32_t stage[NW][512];
+    __shared__ unsigned int base[MAXK];  // next free row of each class in this tile's share
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long t0 = static_cast<long long>(tile) * TILE;
     uint32_t w[NG][4];
     load_tile(labels, t0, P, vec, w);
@@ -302,29 +262,20 @@ __device__ __forceinline__ void tile_compact_body(const uint8_t* __restrict__ la
         for (int c = 0; c < tid; ++c) start += cls_count[c];
         base[tid] = start + tiles[static_cast<long long>(tile) * (K + 1) + tid];
     }
-    unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
-    #pragma unroll
-    for (int u = 0; u < NG; ++u)
-        if ((w[u][0] | w[u][1] | w[u][2] | w[u][3]) != 0u) count16(w[u], K, cnt);
-    unsigned long long excl[4], total[4];
-    block_scan_packed(cnt, (K + 3) >> 2, wsum, excl, total);  // also orders base[] before its reads
-    // class by class: the 16-bit mask of the group's labels equal to c + 1,
-    // then one store per set bit to consecutive rows
+    __syncthreads();
+    // each chunk reserves its rows of every class with one shared-memory
+    // atomic (lane c for class c) and places its pixels by ballots
     #pragma unroll
     for (int u = 0; u < NG; ++u) {
-        if ((w[u][0] | w[u][1] | w[u][2] | w[u][3]) == 0u) continue;
-        const unsigned int p0 = static_cast<unsigned int>(t0 + u * SUB + 16LL * tid);
-        #pragma unroll 1
-        for (int c = 0; c < K; ++c) {
-            const uint32_t pat = static_cast<uint32_t>(c + 1) * 0x01010101u;
-            uint32_t m = 0u;
-            #pragma unroll
-            for (int q = 0; q < 4; ++q) m |= byte_bits(__vcmpeq4(w[u][q], pat)) << (4 * q);
-            if (!m) continue;
-            unsigned int pos = base[c] + field(excl, c);
-            bump_by(excl, c, __popc(m));
-            for (; m; m &= m - 1) list[pos++] = p0 + static_cast<unsigned int>(__ffs(m) - 1);
-        }
+        if (!__any_sync(0xFFFFFFFFu, (w[u][0] | w[u][1] | w[u][2] | w[u][3]) != 0u)) continue;
+        const int T = stage_chunk(w[u], stage[warp], lane);
+        unsigned int mine = 0u;
+        bool over = false;
+        count_staged(stage[warp], T, K, lane, mine, over);
+        const unsigned int run = (lane < K && mine) ? atomicAdd(&base[lane], mine) : 0u;
+        place_staged(stage[warp], T, K, lane, run, static_cast<unsigned long long>(t0 + u * SUB + 512 * warp), list,
+                     0, 0x7FFFFFFFFFFFFFFFll);
+        __syncwarp();  // the stage is rewritten by the next chunk
     }
 }
 
@@ -419,7 +370,6 @@ k_label_scan(const uint8_t* __restrict__ labels, long long P, int K, int vec, lo
 {
     __shared__ uint32_t stage[NW][512];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t below = (1u << lane) - 1u;
     const long long nchunk = (P + 511) / 512;
     const long long wid = (static_cast<long long>(blockIdx.x) * TPB + threadIdx.x) >> 5;
     const long long nw = (static_cast<long long>(gridDim.x) * TPB) >> 5;
@@ -433,43 +383,12 @@ k_label_scan(const uint8_t* __restrict__ labels, long long P, int K, int vec, lo
         if (ch + nw < nchunk) next = chunk_load(labels, P, vec, ch + nw, lane);
         if (!__any_sync(0xFFFFFFFFu, (x.x | x.y | x.z | x.w) != 0u)) continue;
         const uint32_t w[4] = {x.x, x.y, x.z, x.w};
-        int T = 0;  // entries staged, in (byte position, lane) order
-        #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const uint32_t v = (w[j >> 2] >> (8 * (j & 3))) & 0xFFu;
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v != 0u);
-            if (bal) {
-                if (v) st[T + __popc(bal & below)] = static_cast<uint32_t>(16 * lane + j) | (v << 16);
-                T += __popc(bal);
-            }
-        }
-        __syncwarp();
+        const int T = stage_chunk(w, st, lane);
         unsigned int mine = 0u;  // lane c: the chunk's count of class c
-        for (int i0 = 0; i0 < T; i0 += 32) {
-            const uint32_t v = (i0 + lane < T) ? (st[i0 + lane] >> 16) : 0u;
-            bad |= v > static_cast<uint32_t>(K);
-            for (int c = 0; c < K; ++c) {
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v == static_cast<uint32_t>(c + 1));
-                if (lane == c) mine += __popc(bal);
-            }
-        }
-        unsigned int run = 0u;   // lane c: the next row of class c
-        if (lane < K && mine) run = atomicAdd(&dm->cls_count[lane], mine);
-        for (int i0 = 0; i0 < T; i0 += 32) {
-            const uint32_t e = (i0 + lane < T) ? st[i0 + lane] : 0u;
-            const uint32_t v = e >> 16;
-            for (int c = 0; c < K; ++c) {
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v == static_cast<uint32_t>(c + 1));
-                const unsigned int base = __shfl_sync(0xFFFFFFFFu, run, c);
-                if (v == static_cast<uint32_t>(c + 1)) {
-                    const unsigned long long pos = static_cast<unsigned long long>(base) + __popc(bal & below);
-                    if (pos < static_cast<unsigned long long>(cap))
-                        list[static_cast<long long>(c) * cap + static_cast<long long>(pos)] =
-                            static_cast<unsigned int>(ch * 512 + (e & 0xFFFFu));
-                }
-                if (lane == c) run += __popc(bal);
-            }
-        }
+        count_staged(st, T, K, lane, mine, bad);
+        // lane c reserves class c's rows (all classes' atomics in flight together)
+        const unsigned int run = (lane < K && mine) ? atomicAdd(&dm->cls_count[lane], mine) : 0u;
+        place_staged(st, T, K, lane, run, static_cast<unsigned long long>(ch * 512), list, cap, cap);
         __syncwarp();  // the staging area is rewritten by the next chunk
     }
     if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicCAS(&dm->status, 0, CVA_ERR_LABEL_RANGE);
