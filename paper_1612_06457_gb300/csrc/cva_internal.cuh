@@ -119,8 +119,9 @@ __host__ __device__ inline int xtr_row(int B)
 
 // Training-pixel passes: a reset, one pass over the labels writing every
 // training pixel's index to its class's region of `list` (K regions of `cap`
-// entries), the gather of every training pixel's bands into the class-major
-// matrix `xtr` (`cap` rows of xtr_row(B)), then the exact moments from it.
+// entries), then one pass that gathers every training pixel's bands into the
+// class-major matrix `xtr` (`cap` rows of xtr_row(B)) and forms the exact
+// moments from them in the same CTA.
 cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const uint8_t* labels,
                                int K, DevModel* dm, uint16_t* xtr, unsigned int* list,
                                long long cap, int num_sms, cudaStream_t s);

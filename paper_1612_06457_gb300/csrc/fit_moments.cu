@@ -9,28 +9,32 @@
 // depend on the order of accumulation, so the result is deterministic even
 // though thread blocks merge their partial sums with atomics.
 //
-// Four passes for one page after a one-CTA reset (k_fit_reset):
-//   k_label_scan    one pass over the labels: each warp takes 512 labels at
-//                   a time (one 16-byte load a lane) and, converged, stages
-//                   the labelled ones in shared memory by ballots, counts
-//                   them by class with one ballot per class, reserves their
-//                   rows with one atomic per class (lane c for class c) and
-//                   writes every pixel index to its class's region of the
-//                   list (class c at list + c cap, in no fixed order);
-//   k_gather        one thread per listed pixel, all band loads in flight:
-//                   the augmented row (x_0 .. x_{B-1}, 1, 0 ..) of the
-//                   class-major training matrix (16-byte rows);
-//   k_moments       exact moments on the tensor cores, in units of up to 256
-//                   rows of one class (see the kernel).  Sums stay in
-//                   registers while a CTA stays on one class and are merged
-//                   into the model with 64-bit integer atomics when it moves
-//                   on.  The "1" column yields n_c and s_c in the same pass.
+// Two passes for one page after a one-CTA reset (k_fit_reset):
+//   k_label_scan      one pass over the labels: each warp takes 512 labels at
+//                     a time (one 16-byte load a lane) and, converged, stages
+//                     the labelled ones in shared memory by ballots, counts
+//                     them by class with one ballot per class, reserves their
+//                     rows with one atomic per class (lane c for class c) and
+//                     writes every pixel index to its class's region of the
+//                     list (class c at list + c cap, in no fixed order);
+//   k_gather_moments  one CTA per unit of up to 256 training rows of one
+//                     class: the rows' bands gathered from the cube (one pixel
+//                     a thread, all band loads in flight), written to the
+//                     class-major training matrix (16-byte rows
+//                     (x_0 .. x_{B-1}, 1, 0 ..), read by the training-range
+//                     pass) and, split into bytes, to shared memory, then the
+//                     exact moments on the tensor cores (see the kernel).
+//                     Sums stay in registers while a CTA stays on one class
+//                     and are merged into the model with 64-bit integer
+//                     atomics when it moves on.  The "1" column yields n_c
+//                     and s_c in the same pass.
 // Training pixels are a small share of a page, so loops of each lane over its
 // own labels would leave most lanes idle: the label passes stay converged on
 // the warp and their cost is the labels' one read plus a little work per
 // chunk that holds a training pixel.
 // The same passes in batched form (kb_*: the flattened work of many pages,
-// see batch.cu), where the training lists are sized exactly: a count pass
+// see batch.cu; there the gather and the moments are separate passes over the
+// pooled rows), where the training lists are sized exactly: a count pass
 // over tiles of 16384 labels (the same staged chunks; each page's last CTA
 // takes the prefix sums over its tiles) and a compaction pass that reserves
 // each chunk's rows inside its tile's share with shared-memory atomics; and
@@ -363,7 +367,7 @@ __device__ __forceinline__ uint4 chunk_load(const uint8_t* __restrict__ labels, 
 // The moments are exact integer sums and the ranges minima and maxima, so
 // nothing downstream depends on the order.  A label above K sets
 // CVA_ERR_LABEL_RANGE and is not listed; entries beyond cap are dropped (the
-// gather then reports CVA_ERR_CAPACITY).
+// gather-moments pass then reports CVA_ERR_CAPACITY).
 __global__ void __launch_bounds__(TPB)
 k_label_scan(const uint8_t* __restrict__ labels, long long P, int K, int vec, long long cap,
              unsigned int* __restrict__ list, DevModel* __restrict__ dm)
@@ -392,40 +396,6 @@ k_label_scan(const uint8_t* __restrict__ labels, long long P, int K, int vec, lo
         __syncwarp();  // the staging area is rewritten by the next chunk
     }
     if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicCAS(&dm->status, 0, CVA_ERR_LABEL_RANGE);
-}
-
-// One thread per training row: rows are class-major (class c from the sum
-// of the counts of the classes before it), each taken from its class's
-// region of the list.
-__global__ void __launch_bounds__(TPB)
-k_gather(const uint16_t* __restrict__ cube, int B, long long P, int K, const unsigned int* __restrict__ list,
-         long long cap, uint16_t* __restrict__ xtr, DevModel* __restrict__ dm)
-{
-    __shared__ unsigned int start[MAXK + 1];
-    __shared__ unsigned long long total;
-    if (dm->status != 0) return;
-    if (threadIdx.x == 0) {
-        unsigned long long n = 0;
-        start[0] = 0u;
-        #pragma unroll 1
-        for (int c = 0; c < K; ++c) {
-            n += dm->cls_count[c];
-            start[c + 1] = static_cast<unsigned int>(n < 0xFFFFFFFFull ? n : 0xFFFFFFFFull);
-        }
-        total = n;
-    }
-    __syncthreads();
-    const unsigned long long N = total;
-    if (N > static_cast<unsigned long long>(cap)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&dm->status, 0, CVA_ERR_CAPACITY);
-        return;
-    }
-    const unsigned int stride = gridDim.x * TPB;
-    for (unsigned int i = blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
-        int c = 0;
-        while (i >= start[c + 1]) ++c;
-        gather_row(cube, B, P, list[static_cast<long long>(c) * cap + (i - start[c])], xtr, i);
-    }
 }
 
 // ldmatrix / mma.sync wrappers (bf16 inputs, f32 accumulators)
@@ -598,16 +568,31 @@ __device__ __forceinline__ void moments_unit(uint16_t* XT, float* Cs, const uint
 // is recombined in 64-bit integers.  Each thread owns up to three (a <= b)
 // entries of the augmented moment matrix and keeps them in registers while
 // the CTA stays on one class.
-__global__ void __launch_bounds__(TPB, 6)
-k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevModel* __restrict__ dm)
+//
+// For one page the gather is fused with the moments: one CTA per unit of up
+// to 256 training rows of one class, and thread t takes the unit's pixel t
+// straight from the cube (all NBAND band loads in flight, with the 64-byte
+// fetch hint of the gather), writes its augmented row to the training matrix
+// (which the training-range pass reads) and its bytes to the transposed unit
+// in shared memory, from which the Gram matrix is formed.  Against a gather
+// pass and a moments pass (18 + 12.4 us under ncu on the benchmark page) it
+// takes 23.5-24.8 us: one launch and the training matrix's re-read fewer.  NBAND
+// (24 or MAXB) bounds B, so that the 23-band case keeps 24 values a thread:
+// 48 registers, five CTAs an SM (with six the values spill); four above 24.
+__host__ __device__ constexpr int gm_ctas(int NBAND) { return NBAND <= 24 ? 5 : 4; }
+
+template <int NBAND>
+__global__ void __launch_bounds__(TPB, gm_ctas(NBAND))
+k_gather_moments(const uint16_t* __restrict__ cube, int B, long long P, int K, const unsigned int* __restrict__ list,
+                 long long cap, uint16_t* __restrict__ xtr, DevModel* __restrict__ dm)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ unsigned int ustart[MAXK + 1], cstart[MAXK], ccount[MAXK];
     __shared__ unsigned char pa[MAXPAIR], pb[MAXPAIR];
     __shared__ int stop;
 
-    const int F = xtr_row(B);       // padded augmented width (multiple of 8)
-    const int F2 = 2 * F;           // rows of the split matrix (multiple of 16)
+    const int F = xtr_row(B);
+    const int F2 = 2 * F;
     const int BA = B + 1;
     const int npair = BA * (BA + 1) / 2;
     const int nb = mom_shape(B).nb;
@@ -628,7 +613,9 @@ k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevMode
             units += (n + UNIT - 1) / UNIT;
         }
         ustart[K] = units;
-        stop = (dm->status != 0) || (tot > static_cast<unsigned long long>(cap));
+        const bool over = tot > static_cast<unsigned long long>(cap);
+        stop = (dm->status != 0) || over;
+        if (over && blockIdx.x == 0) atomicCAS(&dm->status, 0, CVA_ERR_CAPACITY);
     }
     build_pairs(pa, pb, BA);
     __syncthreads();
@@ -646,7 +633,38 @@ k_moments(int B, int K, const uint16_t* __restrict__ xtr, long long cap, DevMode
         }
         const unsigned int row0 = cstart[c] + (u - ustart[c]) * UNIT;
         const int len = static_cast<int>(min(static_cast<unsigned int>(UNIT), cstart[c] + ccount[c] - row0));
-        moments_unit(XT, Cs, xtr, F, row0, len, npair, pa, pb, acc);
+        const bool live = tid < len;
+        uint32_t xv[NBAND];
+        if (live) {
+            const unsigned int pix = list[static_cast<long long>(c) * cap + (row0 - cstart[c]) + tid];
+            const uint16_t* src = cube + pix;
+            #pragma unroll
+            for (int b = 0; b < NBAND; ++b) xv[b] = (b < B) ? ld_u16_l2_64(src + static_cast<long long>(b) * P) : 0u;
+        } else {
+            #pragma unroll
+            for (int b = 0; b < NBAND; ++b) xv[b] = 0u;
+        }
+        uint4* grow = reinterpret_cast<uint4*>(xtr + static_cast<long long>(row0 + tid) * F);
+        #pragma unroll
+        for (int q = 0; q < (NBAND + 8) / 8; ++q) {
+            if (q * 8 < F) {
+                uint32_t pk[4];
+                #pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                    const int f = q * 8 + h;
+                    // the augmented row: x_0 .. x_{B-1}, 1, zeros; a row past the unit's end is all zero
+                    uint32_t v = (f < B) ? xv[f < NBAND ? f : 0] : (f == B ? 1u : 0u);
+                    if (!live) v = 0u;
+                    if (h & 1) pk[h >> 1] |= v << 16;
+                    else pk[h >> 1] = v;
+                    XT[f * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(v >> 8));
+                    XT[(F + f) * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(v & 0xFFu));
+                }
+                if (live) grow[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+        __syncthreads();
+        moments_gram(XT, Cs, F, npair, pa, pb, acc);
     }
     if (cur_class >= 0) moments_flush(dm, cur_class, nb, npair, pa, pb, acc);
 }
@@ -1148,21 +1166,22 @@ cudaError_t launch_fit_moments(const uint16_t* cube, int B, long long P, const u
     k_label_scan<<<static_cast<unsigned>(num_sms * 8), TPB, 0, s>>>(labels, P, K, vec, cap, list, dm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_gather<<<static_cast<unsigned>(num_sms * 8), TPB, 0, s>>>(cube, B, P, K, list, cap, xtr, dm);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-
     const int F2 = 2 * xtr_row(B);
     const size_t smem = moments_smem_bytes(F2 / 2);
-    e = cudaFuncSetAttribute(k_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    // the unit count is only known on the device: size the grid for the
-    // useful maximum and let idle CTAs exit at once.  Six CTAs an SM (40
-    // registers, ~36 KB of shared memory each) are resident together, so up
-    // to 6 x SMs units (912 on 152 SMs; 784 on the 23-band benchmark page)
-    // each take one CTA instead of two rounds
-    const long long g3 = static_cast<long long>(num_sms) * 6;
-    k_moments<<<static_cast<unsigned>(g3), TPB, smem, s>>>(B, K, xtr, cap, dm);
+    // the unit count is only known on the device: one wave of resident CTAs
+    // (five an SM up to 24 bands, ~36 KB of shared memory each), each taking
+    // units in turn; CTAs without a unit exit at once
+    if (B <= 24) {
+        e = cudaFuncSetAttribute(k_gather_moments<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        k_gather_moments<24><<<static_cast<unsigned>(num_sms * gm_ctas(24)), TPB, smem, s>>>(cube, B, P, K, list, cap,
+                                                                                               xtr, dm);
+    } else {
+        e = cudaFuncSetAttribute(k_gather_moments<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        k_gather_moments<MAXB><<<static_cast<unsigned>(num_sms * gm_ctas(MAXB)), TPB, smem, s>>>(cube, B, P, K, list,
+                                                                                                   cap, xtr, dm);
+    }
     return cudaGetLastError();
 }
 
