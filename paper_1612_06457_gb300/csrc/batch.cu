@@ -20,8 +20,8 @@
 //                      pooled matrix words, moment units and range items;
 //                      capacity check of the pooled training storage
 //   kb_tile_compact    class-major training lists, one per page, in the pool
-//   kb_gather          the pooled training matrix
-//   kb_moments         exact moments on the tensor cores
+//   kb_gather_moments  the pooled training matrix, gathered unit by unit,
+//                      and its exact moments on the tensor cores
 //   kb_fit_finalize    one CTA per page
 //   kb_train_range<k>  training-score ranges
 //   kb_project_v8<k>   fused projection + 8-bit rescale (persistent)
@@ -366,8 +366,8 @@ cudaError_t run_batch(cva_batch* b, int n, const Plan& plan, cudaStream_t s, boo
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cva::launch_batch_tile_compact(b->pages, b->tile_page, plan.tiles_total, b->list, s);
-    if (e == cudaSuccess) e = cva::launch_batch_gather(b->pages, n, b->tot, b->list, b->xtr, b->num_sms, s);
-    if (e == cudaSuccess) e = cva::launch_batch_moments(b->pages, n, b->tot, b->xtr, plan.max_b, b->num_sms, s);
+    if (e == cudaSuccess)
+        e = cva::launch_batch_gather_moments(b->pages, n, b->tot, b->list, b->xtr, plan.max_b, b->num_sms, s);
     if (e == cudaSuccess) e = cva::launch_batch_finalize(b->pages, n, s);
     if (e == cudaSuccess)
         e = cva::launch_batch_train_range(b->pages, n, b->tot, b->xtr, plan.max_k, b->num_sms, s);

@@ -233,10 +233,9 @@ cudaError_t launch_batch_tile_count(const PageDev* pages, const int* tile_page, 
                                     cudaStream_t s);
 cudaError_t launch_batch_tile_compact(const PageDev* pages, const int* tile_page, long long ntiles_total,
                                       unsigned int* list_pool, cudaStream_t s);
-cudaError_t launch_batch_gather(const PageDev* pages, int n, const BatchTotals* tot, const unsigned int* list_pool,
-                                uint16_t* xtr_pool, int num_sms, cudaStream_t s);
-cudaError_t launch_batch_moments(const PageDev* pages, int n, const BatchTotals* tot, const uint16_t* xtr_pool,
-                                 int max_b, int num_sms, cudaStream_t s);
+cudaError_t launch_batch_gather_moments(const PageDev* pages, int n, const BatchTotals* tot,
+                                       const unsigned int* list_pool, uint16_t* xtr_pool, int max_b, int num_sms,
+                                       cudaStream_t s);
 cudaError_t launch_batch_finalize(const PageDev* pages, int n, cudaStream_t s);
 cudaError_t launch_batch_train_range(const PageDev* pages, int n, const BatchTotals* tot,
                                      const uint16_t* xtr_pool, int max_k, int num_sms, cudaStream_t s);

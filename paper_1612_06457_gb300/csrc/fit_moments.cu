@@ -33,8 +33,7 @@
 // the warp and their cost is the labels' one read plus a little work per
 // chunk that holds a training pixel.
 // The same passes in batched form (kb_*: the flattened work of many pages,
-// see batch.cu; there the gather and the moments are separate passes over the
-// pooled rows), where the training lists are sized exactly: a count pass
+// see batch.cu), where the training lists are sized exactly: a count pass
 // over tiles of 16384 labels (the same staged chunks; each page's last CTA
 // takes the prefix sums over its tiles) and a compaction pass that reserves
 // each chunk's rows inside its tile's share with shared-memory atomics; and
@@ -296,33 +295,6 @@ __device__ inline uint32_t ld_u16_l2_64(const uint16_t* p)
     return v;
 }
 
-// The augmented row (x_0 .. x_{B-1}, 1, 0 ..) of listed training pixel i,
-// all its band loads in flight, stored as one 16-byte-aligned row.
-__device__ __forceinline__ void gather_row(const uint16_t* __restrict__ cube, int B, long long P, unsigned int pix,
-                                           uint16_t* __restrict__ xtr, unsigned int i)
-{
-    const int BR = xtr_row(B);
-    const uint16_t* src = cube + pix;
-    uint32_t xv[MAXB];
-    #pragma unroll
-    for (int b = 0; b < MAXB; ++b) xv[b] = (b < B) ? ld_u16_l2_64(src + static_cast<long long>(b) * P) : 0u;
-    uint4* grow = reinterpret_cast<uint4*>(xtr + static_cast<long long>(i) * BR);
-    #pragma unroll
-    for (int q = 0; q < (MAXB + 8) / 8; ++q) {
-        if (q * 8 < BR) {
-            uint32_t pk[4];
-            #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int b0 = q * 8 + 2 * h, b1 = b0 + 1;
-                const uint32_t v0 = (b0 < B) ? xv[b0 < MAXB ? b0 : 0] : (b0 == B ? 1u : 0u);
-                const uint32_t v1 = (b1 < B) ? xv[b1 < MAXB ? b1 : 0] : (b1 == B ? 1u : 0u);
-                pk[h] = v0 | (v1 << 16);
-            }
-            grow[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        }
-    }
-}
-
 // The fit's state before the label scan: moments and class counters zero,
 // status clear, model not fitted (one CTA).
 __global__ void k_fit_reset(DevModel* __restrict__ dm, int B, int K)
@@ -526,36 +498,46 @@ __device__ __forceinline__ void moments_gram(const uint16_t* XT, float* Cs, int 
     __syncthreads();
 }
 
-// One unit: rows [row0, row0 + len) of the training matrix (row length F)
-// split into bytes, transposed into shared memory, its Gram matrix formed on
-// the tensor cores and added to the thread's moment sums.  Every thread of
-// the CTA takes part (three barriers).
-__device__ __forceinline__ void moments_unit(uint16_t* XT, float* Cs, const uint16_t* __restrict__ xtr, int F,
-                                             unsigned int row0, int len, int npair, const unsigned char* pa,
-                                             const unsigned char* pb, unsigned long long (&acc)[3])
+// One unit's training pixels gathered and staged: thread t < len takes
+// pixel ulist[t] of the cube (all band loads in flight, with the gather's
+// 64-byte fetch hint), writes its augmented row (x_0 .. x_{B-1}, 1, zeros) to
+// rows + t F and its bytes to the transposed unit XT; threads from len on
+// stage zero columns.  NBAND (24 or MAXB) bounds B.  The caller
+// synchronizes before XT is read.
+template <int NBAND>
+__device__ __forceinline__ void gather_stage(uint16_t* XT, const uint16_t* __restrict__ cube, int B, long long P,
+                                             const unsigned int* __restrict__ ulist, uint16_t* __restrict__ rows,
+                                             int F, int len)
 {
     const int tid = threadIdx.x;
-    // split and transpose: thread tid owns pixel column tid of the unit
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(xtr + static_cast<long long>(row0 + tid) * F);
+    const bool live = tid < len;
+    uint32_t xv[NBAND];
+    if (live) {
+        const uint16_t* src = cube + ulist[tid];
         #pragma unroll
-        for (int q = 0; q < (MAXB + 8) / 8; ++q) {
-            if (q * 8 < F) {
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (tid < len) v = __ldg(src + q);
-                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-                #pragma unroll
-                for (int h = 0; h < 8; ++h) {
-                    const uint32_t x = (wv[h >> 1] >> (16 * (h & 1))) & 0xFFFFu;
-                    const int f = q * 8 + h;
-                    XT[f * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x >> 8));
-                    XT[(F + f) * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(x & 0xFFu));
-                }
+        for (int b = 0; b < NBAND; ++b) xv[b] = (b < B) ? ld_u16_l2_64(src + static_cast<long long>(b) * P) : 0u;
+    } else {
+        #pragma unroll
+        for (int b = 0; b < NBAND; ++b) xv[b] = 0u;
+    }
+    uint4* grow = reinterpret_cast<uint4*>(rows + static_cast<long long>(tid) * F);
+    #pragma unroll
+    for (int q = 0; q < (NBAND + 8) / 8; ++q) {
+        if (q * 8 < F) {
+            uint32_t pk[4];
+            #pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const int f = q * 8 + h;
+                uint32_t v = (f < B) ? xv[f < NBAND ? f : 0] : (f == B ? 1u : 0u);
+                if (!live) v = 0u;
+                if (h & 1) pk[h >> 1] |= v << 16;
+                else pk[h >> 1] = v;
+                XT[f * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(v >> 8));
+                XT[(F + f) * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(v & 0xFFu));
             }
+            if (live) grow[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
     }
-    __syncthreads();
-    moments_gram(XT, Cs, F, npair, pa, pb, acc);
 }
 
 // Exact moments on the tensor cores.  A unit holds up to 256 training rows of
@@ -633,36 +615,8 @@ k_gather_moments(const uint16_t* __restrict__ cube, int B, long long P, int K, c
         }
         const unsigned int row0 = cstart[c] + (u - ustart[c]) * UNIT;
         const int len = static_cast<int>(min(static_cast<unsigned int>(UNIT), cstart[c] + ccount[c] - row0));
-        const bool live = tid < len;
-        uint32_t xv[NBAND];
-        if (live) {
-            const unsigned int pix = list[static_cast<long long>(c) * cap + (row0 - cstart[c]) + tid];
-            const uint16_t* src = cube + pix;
-            #pragma unroll
-            for (int b = 0; b < NBAND; ++b) xv[b] = (b < B) ? ld_u16_l2_64(src + static_cast<long long>(b) * P) : 0u;
-        } else {
-            #pragma unroll
-            for (int b = 0; b < NBAND; ++b) xv[b] = 0u;
-        }
-        uint4* grow = reinterpret_cast<uint4*>(xtr + static_cast<long long>(row0 + tid) * F);
-        #pragma unroll
-        for (int q = 0; q < (NBAND + 8) / 8; ++q) {
-            if (q * 8 < F) {
-                uint32_t pk[4];
-                #pragma unroll
-                for (int h = 0; h < 8; ++h) {
-                    const int f = q * 8 + h;
-                    // the augmented row: x_0 .. x_{B-1}, 1, zeros; a row past the unit's end is all zero
-                    uint32_t v = (f < B) ? xv[f < NBAND ? f : 0] : (f == B ? 1u : 0u);
-                    if (!live) v = 0u;
-                    if (h & 1) pk[h >> 1] |= v << 16;
-                    else pk[h >> 1] = v;
-                    XT[f * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(v >> 8));
-                    XT[(F + f) * UPAD + tid] = static_cast<uint16_t>(bf16_of_byte(v & 0xFFu));
-                }
-                if (live) grow[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            }
-        }
+        gather_stage<NBAND>(XT, cube, B, P, list + static_cast<long long>(c) * cap + (row0 - cstart[c]),
+                            xtr + static_cast<long long>(row0) * F, F, len);
         __syncthreads();
         moments_gram(XT, Cs, F, npair, pa, pb, acc);
     }
@@ -693,27 +647,16 @@ kb_tile_compact(const PageDev* __restrict__ pages, const int* __restrict__ tile_
                       static_cast<int>(blockIdx.x - pg.tile0));
 }
 
-// One thread per pooled training row; rows of failed pages are skipped.
-__global__ void __launch_bounds__(TPB)
-kb_gather(const PageDev* __restrict__ pages, int n, const BatchTotals* __restrict__ tot,
-          const unsigned int* __restrict__ list_pool, uint16_t* __restrict__ xtr_pool)
-{
-    const unsigned long long rows = tot->rows;
-    const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * TPB;
-    for (unsigned long long r = static_cast<unsigned long long>(blockIdx.x) * TPB + threadIdx.x; r < rows; r += stride) {
-        const int p = find_page(pages, n, r, [](const PageDev& q) { return q.row0; });
-        const PageDev& pg = pages[p];
-        if (pg.dm->status != 0) continue;
-        gather_row(pg.cube, pg.B, pg.P, list_pool[r], xtr_pool + pg.xoff, static_cast<unsigned int>(r - pg.row0));
-    }
-}
-
 // Moment units of all pages: a unit is up to 256 rows of one class of one
-// page.  A CTA keeps its sums in registers while it stays on one (page,
-// class) and merges them into that page's model when it moves on.
-__global__ void __launch_bounds__(TPB)
-kb_moments(const PageDev* __restrict__ pages, int n, const BatchTotals* __restrict__ tot,
-           const uint16_t* __restrict__ xtr_pool, int max_f)
+// page, gathered from the page's cube and staged as in k_gather_moments (the
+// rows also go to the pooled training matrix, which the training-range pass
+// reads).  A CTA keeps its sums in registers while it stays on one (page,
+// class) and merges them into that page's model when it moves on.  NBAND (24
+// or MAXB) bounds the batch's band counts.
+template <int NBAND>
+__global__ void __launch_bounds__(TPB, 4)
+kb_gather_moments(const PageDev* __restrict__ pages, int n, const BatchTotals* __restrict__ tot,
+                  const unsigned int* __restrict__ list_pool, uint16_t* __restrict__ xtr_pool, int max_f)
 {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ unsigned char pa[MAXPAIR], pb[MAXPAIR];
@@ -781,8 +724,15 @@ kb_moments(const PageDev* __restrict__ pages, int n, const BatchTotals* __restri
             cur_class = c;
             cur_b = B;
         }
-        if (!s_skip) moments_unit(XT, Cs, xtr_pool + pg.xoff, xtr_row(B), s_row0, s_len, npair, pa, pb, acc);
-        else __syncthreads();
+        if (!s_skip) {
+            const int F = xtr_row(B);
+            gather_stage<NBAND>(XT, pg.cube, B, pg.P, list_pool + pg.row0 + s_row0,
+                                xtr_pool + pg.xoff + static_cast<long long>(s_row0) * F, F, s_len);
+            __syncthreads();
+            moments_gram(XT, Cs, F, npair, pa, pb, acc);
+        } else {
+            __syncthreads();
+        }
     }
     if (cur_page >= 0)
         moments_flush(pages[cur_page].dm, cur_class, mom_shape(cur_b).nb, (cur_b + 1) * (cur_b + 2) / 2, pa, pb, acc);
@@ -1203,21 +1153,24 @@ cudaError_t launch_batch_tile_compact(const PageDev* pages, const int* tile_page
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_gather(const PageDev* pages, int n, const BatchTotals* tot, const unsigned int* list_pool,
-                                uint16_t* xtr_pool, int num_sms, cudaStream_t s)
-{
-    kb_gather<<<static_cast<unsigned>(num_sms * 8), TPB, 0, s>>>(pages, n, tot, list_pool, xtr_pool);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_batch_moments(const PageDev* pages, int n, const BatchTotals* tot, const uint16_t* xtr_pool,
-                                 int max_b, int num_sms, cudaStream_t s)
+cudaError_t launch_batch_gather_moments(const PageDev* pages, int n, const BatchTotals* tot,
+                                       const unsigned int* list_pool, uint16_t* xtr_pool, int max_b, int num_sms,
+                                       cudaStream_t s)
 {
     const int F = xtr_row(max_b);
     const size_t smem = moments_smem_bytes(F);
-    cudaError_t e = cudaFuncSetAttribute(kb_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    kb_moments<<<static_cast<unsigned>(num_sms * 4), TPB, smem, s>>>(pages, n, tot, xtr_pool, F);
+    cudaError_t e;
+    if (max_b <= 24) {
+        e = cudaFuncSetAttribute(kb_gather_moments<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        kb_gather_moments<24><<<static_cast<unsigned>(num_sms * 4), TPB, smem, s>>>(pages, n, tot, list_pool, xtr_pool, F);
+    } else {
+        e = cudaFuncSetAttribute(kb_gather_moments<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        kb_gather_moments<MAXB><<<static_cast<unsigned>(num_sms * 4), TPB, smem, s>>>(pages, n, tot, list_pool, xtr_pool,
+                                                                                       F);
+    }
     return cudaGetLastError();
 }
 
