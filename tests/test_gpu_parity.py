@@ -89,6 +89,8 @@ CASES = [
     (107, 32, 96, 128, 5, (900, 800, 700, 600, 500), 4),
     (108, 20, 1, 4096, 3, (300, 200, 100), 2),            # a single row
     (109, 8, 4096, 1, 2, (300, 200), 1),                  # a single column
+    (110, 24, 96, 120, 3, (900, 700, 500), 2),            # 24 bands: the widest of the 24-value gather
+    (111, 25, 96, 120, 4, (900, 700, 500, 400), 3),       # 25: the narrowest of the 32-value gather
 ]
 
 
