@@ -233,3 +233,30 @@ def test_fit_alone_then_projection_equals_the_whole_batch_call():
         np.testing.assert_array_equal(p[4].cpu().numpy(), u)
         np.testing.assert_array_equal(p[5].cpu().numpy(), lam)
     b.close()
+
+
+def test_densely_labelled_pages_in_sixteen_classes():
+    """Pages labelled everywhere (each pixel with its class, up to 16 classes;
+    the batch projects at most 8 variates a page) beside a sparsely labelled one: the batched label passes then stage full
+    512-label chunks in every class, and each chunk reserves its rows of the
+    tile's share.  Every page bit-identical to the single-page path."""
+    _skip_without_gpu()
+    import dataclasses
+
+    ws = []
+    for i, (B, H, W, K) in enumerate(((20, 160, 208, 16), (9, 128, 96, 5))):
+        w = make_workload(7700 + i, B, H, W, K, tuple([150] * K), min(K - 1, 5), separation=(1.0, 4.0))
+        lab = (w.classmap + 1).astype(np.uint8)
+        ws.append(dataclasses.replace(w, labels=lab, n_train=tuple(int((lab == c + 1).sum()) for c in range(K))))
+    ws.append(make_workload(7702, 12, 256, 256, 3, (800, 600, 400), 2, separation=(1.0, 4.0), both=False))
+    assert all(min(w.n_train) > w.B for w in ws)
+    pages = _pages(ws)
+    b = cva.Batch(len(ws), sum(w.P for w in ws), sum(sum(w.n_train) for w in ws) + 1024)
+    cva.cva_fit_project_batched(b, pages)
+    st = cva.cva_batch_status(b, len(ws))
+    assert (st == cva.CVA_OK).all(), st
+    for i, (w, p) in enumerate(zip(ws, pages)):
+        u_ref, lam_ref, _, _ = _single(w, p[0], p[1])
+        np.testing.assert_array_equal(p[4].cpu().numpy(), u_ref, err_msg=f"page {i}")
+        np.testing.assert_array_equal(p[5].cpu().numpy(), lam_ref, err_msg=f"page {i}")
+    b.close()
