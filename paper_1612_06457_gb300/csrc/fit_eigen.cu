@@ -122,6 +122,18 @@ __device__ inline unsigned long long mom_get(const DevModel* dm, const MomShape&
     return dm->mom[c][blk_index(i >> 2, j >> 2, sh.nb)][(i & 3) * 4 + (j & 3)];
 }
 
+// The same entry from a shared-memory copy of classes 0 .. K-1 (class c at
+// m + c nblk 16, in the model's block layout).
+__device__ inline unsigned long long mom_s(const unsigned long long* m, const MomShape& sh, int c, int i, int j)
+{
+    if (i > j) { const int t = i; i = j; j = t; }
+    return m[(c * sh.nblk + blk_index(i >> 2, j >> 2, sh.nb)) * 16 + (i & 3) * 4 + (j & 3)];
+}
+
+// Words of the finalize's shared-memory copy of the moments (every class at
+// the largest band count).
+constexpr int MOM_COPY_WORDS = MAXK * MAXBLK * 16;
+
 __device__ inline float warp_sumf(float v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
@@ -583,18 +595,26 @@ __device__ void complete_basis(FinSmem& sm, int B, int j0, int j1)
 }
 
 template <int SER>
-__device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restrict__ dm, int B, int K, int nvec)
+__device__ __forceinline__ void fit_finalize_body(FinSmem& sm, unsigned long long* __restrict__ mom, DevModel* __restrict__ dm,
+                                                  int B, int K, int nvec)
 {
     const MomShape sh = mom_shape(B);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (dm->status != 0) return;  // an earlier pass already failed
+    // the exact moments of the K classes into shared memory, all loads at once
+    // (the phases below read them many times, in dependent loops)
+    for (int q = tid; q < K * sh.nblk * 16; q += TPB) {
+        const int c = q / (sh.nblk * 16), r = q - c * (sh.nblk * 16);
+        mom[q] = dm->mom[c][r >> 4][r & 15];
+    }
+    __syncthreads();
 
     // ---- 0. counts, totals, triangle tables ---------------------------------
-    if (tid < K) sm.n[tid] = mom_get(dm, sh, tid, B, B);
+    if (tid < K) sm.n[tid] = mom_s(mom, sh, tid, B, B);
     if (tid < B) {
         unsigned long long t = 0;
         #pragma unroll 1
-        for (int c = 0; c < K; ++c) t += mom_get(dm, sh, c, tid, B);
+        for (int c = 0; c < K; ++c) t += mom_s(mom, sh, c, tid, B);
         sm.tot[tid] = t;
     }
     for (int i = warp; i < MAXB; i += NWARP)
@@ -630,7 +650,7 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
     // ---- 1. class means, Sw and Mb from exact numerators ----------------------
     for (int e = tid; e < K * B; e += TPB) {
         const int c = e / B, b = e - (e / B) * B;
-        const unsigned long long s = mom_get(dm, sh, c, b, B);
+        const unsigned long long s = mom_s(mom, sh, c, b, B);
         dm->mu_c[c][b] = df_to_double(df_mul(df_from_u64(s), sm.invn[c]));
         const __int128 num = static_cast<__int128>(sm.N) * s - static_cast<__int128>(sm.n[c]) * sm.tot[b];
         const df v = df_mul(df_mul(df_mul(df_from_i128(num), sm.invn[c]), sm.invN), sm.sqn[c]);
@@ -647,8 +667,8 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
         df acc = df_from(0.0f);
         #pragma unroll 1
         for (int c = 0; c < K; ++c) {
-            const __int128 num = static_cast<__int128>(sm.n[c]) * mom_get(dm, sh, c, i, l) -
-                                 static_cast<__int128>(mom_get(dm, sh, c, i, B)) * mom_get(dm, sh, c, l, B);
+            const __int128 num = static_cast<__int128>(sm.n[c]) * mom_s(mom, sh, c, i, l) -
+                                 static_cast<__int128>(mom_s(mom, sh, c, i, B)) * mom_s(mom, sh, c, l, B);
             acc = df_add(acc, df_mul(df_from_i128(num), sm.invn[c]));
         }
         sm.A[i][l] = acc;
@@ -941,7 +961,8 @@ __device__ __forceinline__ void fit_finalize_body(FinSmem& sm, DevModel* __restr
 __global__ void __launch_bounds__(TPB) k_fit_finalize(DevModel* __restrict__ dm, int B, int K, int nvec)
 {
     extern __shared__ __align__(16) unsigned char fin_dyn[];
-    fit_finalize_body<8>(*reinterpret_cast<FinSmem*>(fin_dyn), dm, B, K, nvec);
+    fit_finalize_body<8>(*reinterpret_cast<FinSmem*>(fin_dyn),
+                         reinterpret_cast<unsigned long long*>(fin_dyn + sizeof(FinSmem)), dm, B, K, nvec);
 }
 
 // Batched form: one CTA per page, all pages at once; the eigenvalues are
@@ -950,7 +971,8 @@ __global__ void __launch_bounds__(TPB) kb_fit_finalize(const PageDev* __restrict
 {
     extern __shared__ __align__(16) unsigned char fin_dyn[];
     const PageDev& pg = pages[blockIdx.x];
-    fit_finalize_body<8>(*reinterpret_cast<FinSmem*>(fin_dyn), pg.dm, pg.B, pg.K, pg.k);
+    fit_finalize_body<8>(*reinterpret_cast<FinSmem*>(fin_dyn),
+                         reinterpret_cast<unsigned long long*>(fin_dyn + sizeof(FinSmem)), pg.dm, pg.B, pg.K, pg.k);
     __syncthreads();
     if (pg.eigvals && threadIdx.x < pg.B && pg.dm->status == 0) pg.eigvals[threadIdx.x] = pg.dm->lam[threadIdx.x];
 }
@@ -1119,7 +1141,7 @@ __global__ void k_scatter_sb(DevModel* __restrict__ dm, int B, int K)
 
 cudaError_t launch_fit_finalize(DevModel* dm, int B, int K, int nvec, cudaStream_t s)
 {
-    const int smem = static_cast<int>(sizeof(FinSmem));
+    const int smem = static_cast<int>(sizeof(FinSmem) + sizeof(unsigned long long) * K * mom_shape(B).nblk * 16);
     cudaError_t e = cudaFuncSetAttribute(k_fit_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_fit_finalize<<<1, TPB, smem, s>>>(dm, B, K, nvec);
@@ -1128,7 +1150,7 @@ cudaError_t launch_fit_finalize(DevModel* dm, int B, int K, int nvec, cudaStream
 
 cudaError_t launch_batch_finalize(const PageDev* pages, int n, cudaStream_t s)
 {
-    const int smem = static_cast<int>(sizeof(FinSmem));
+    const int smem = static_cast<int>(sizeof(FinSmem) + sizeof(unsigned long long) * MOM_COPY_WORDS);
     cudaError_t e = cudaFuncSetAttribute(kb_fit_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kb_fit_finalize<<<static_cast<unsigned>(n), TPB, smem, s>>>(pages);
