@@ -245,7 +245,6 @@ __device__ __forceinline__ void tile_count_body(const uint8_t* __restrict__ labe
     scan_tiles(ntiles, K, B, cap, tiles, dm);
 }
 
-
 // One tile's training pixels written to their rows of the class-major list.
 // `cls_count` gives the class segment starts, `tiles` each tile's first row
 // within every segment.
